@@ -1,0 +1,266 @@
+"""Multigrid hierarchy, transfer operators, smoothers and V-cycle
+(oracle; test infrastructure only).
+
+Sec. II.E.3 (multigrid meshes): coarse meshes by h-coarsening complete
+sibling families into their parent (surrogate mesh), then restoring 2:1
+balance; a coarse element takes the minimum degree of its children and no
+level is purely p-coarsened.  Sec. II.E.6 (inter-mesh operators): the
+prolongation I_h^H of eq. (psi-interpolation) is nodal interpolation of the
+parent basis at the children's LGL nodes; restriction is its transpose
+(eq. temp-G); the zeroth-order term is restricted as O^H = I^T O^h I
+(eq. operator_oh) while the Laplacian part is re-discretised per level.
+Alg. 3 (V-cycle), Alg. 4 (Chebyshev smoother), Alg. 5 (CG spectral bound).
+
+Readings:
+ * Balancing: a coarsened parent that would touch an element two or more
+   levels finer is un-coarsened (its children kept with their own degrees);
+   repeated to a fixpoint.  The hierarchy ends when no family can be merged.
+ * Alg. 4 update is p <- alpha r + beta p (standard Chebyshev three-term
+   recurrence; the printed minus sign does not give a Chebyshev polynomial).
+ * Alg. 5 eigenvalue estimate: Lanczos tridiagonal from the CG coefficients,
+   T_kk = 1/a_k + b_{k-1}/a_{k-1}, |T_{k,k+1}| = sqrt(b_k)/a_k, and
+   lambda_k = T_kk + |T_{k,k-1}| + |T_{k,k+1}| (Gershgorin row k);
+   lambda_max = max_k lambda_k.  CG stops early when p.Jp <= 0 or r.r = 0;
+   a smoother whose estimate stayed 0 skips its Chebyshev steps.
+ * Level 0 "solve": the smoother (paper) or an exact dense Cholesky solve.
+
+Pins: Chebyshev error polynomial on a diagonal matrix, Gershgorin bound >=
+lambda_max, CG iterates vs textbook CG, prolongation exactness on coarse
+polynomials, restriction/Galerkin identities (tests/test_oracle_multigrid.py).
+"""
+import numpy as np
+import scipy.sparse as sp
+import scipy.linalg as sla
+
+from . import tables
+from .mesh import Mesh
+
+
+def coarsen(mesh):
+    """One coarsening step.  Returns (coarse Mesh, groups) or None.
+
+    groups[H] = list of (fine element, (bx, by, bz)) for a merged family,
+    or [(fine element, None)] for an element carried over unchanged."""
+    leaves = [tuple(int(v) for v in lf) for lf in mesh.leaves]
+    idx = {lf: e for e, lf in enumerate(leaves)}
+    fams = {}
+    for e, (L, i, j, k) in enumerate(leaves):
+        if L == 0:
+            continue
+        fams.setdefault((L - 1, i >> 1, j >> 1, k >> 1), []).append(e)
+    complete = {P for P, ch in fams.items() if len(ch) == 8}
+    if not complete:
+        return None
+    merged = set(complete)
+    while True:
+        cur = {}
+        for lf, e in idx.items():
+            P = (lf[0] - 1, lf[1] >> 1, lf[2] >> 1, lf[3] >> 1) if lf[0] > 0 else None
+            if P in merged:
+                cur[P] = True
+            else:
+                cur[lf] = True
+        cells = set(cur)
+        maxL = max(c[0] for c in cells)
+        undo = set()
+        for P in merged:
+            L, i, j, k = P
+            for d in range(3):
+                for sgn in (-1, 1):
+                    c = [i, j, k]
+                    c[d] += sgn
+                    if c[d] < 0 or c[d] >= (1 << L):
+                        continue
+                    for L2 in range(L + 2, maxL + 1):
+                        sh = L2 - L
+                        span = 1 << sh
+                        lo = [v << sh for v in c]
+                        rng = [range(lo[t], lo[t] + span) for t in range(3)]
+                        rng[d] = [lo[d] + (span - 1 if sgn < 0 else 0)]
+                        if any((L2, a, b, cc) in cells for a in rng[0] for b in rng[1] for cc in rng[2]):
+                            undo.add(P)
+                            break
+                    if P in undo:
+                        break
+                if P in undo:
+                    break
+        if not undo:
+            break
+        merged -= undo
+        if not merged:
+            return None
+    new_leaves, new_p, groups, seen = [], [], [], set()
+    for e, lf in enumerate(leaves):
+        P = (lf[0] - 1, lf[1] >> 1, lf[2] >> 1, lf[3] >> 1) if lf[0] > 0 else None
+        if P in merged:
+            if P in seen:
+                continue
+            seen.add(P)
+            ch = sorted(fams[P])
+            grp = []
+            for c in ch:
+                L, i, j, k = leaves[c]
+                grp.append((c, (i - 2 * P[1], j - 2 * P[2], k - 2 * P[3])))
+            new_leaves.append(P)
+            new_p.append(min(int(mesh.p[c]) for c in ch))
+            groups.append(grp)
+        else:
+            new_leaves.append(lf)
+            new_p.append(int(mesh.p[e]))
+            groups.append([(e, None)])
+    coarse = Mesh(mesh.lo, mesh.hi, new_leaves, new_p, warp=mesh.warp)
+    return coarse, groups
+
+
+def hierarchy(mesh):
+    """Meshes [level 0 (coarsest), ..., level L (= mesh)] and groups per level."""
+    meshes, groups = [mesh], []
+    while True:
+        r = coarsen(meshes[0])
+        if r is None:
+            break
+        meshes.insert(0, r[0])
+        groups.insert(0, r[1])
+    return meshes, groups
+
+
+def child_interp_1d(nH, nh, b):
+    """E[i, a] = l^H_a evaluated at child node i (child half b of the parent)."""
+    xH, _ = tables.lgl_nodes_weights(nH)
+    xh, _ = tables.lgl_nodes_weights(nh)
+    if b is None:
+        return tables.lagrange_values(xH, xh)
+    return tables.lagrange_values(xH, (xh + (2 * b - 1)) / 2.0)
+
+
+def prolongation(fine, coarse, groups):
+    """Sparse I_h^H (fine dofs x coarse dofs) of eq. (psi-interpolation)."""
+    rows, cols, vals = [], [], []
+    for H, grp in enumerate(groups):
+        nH = int(coarse.n[H])
+        for (c, bits) in grp:
+            nh = int(fine.n[c])
+            if bits is None:
+                E = [child_interp_1d(nH, nh, None)] * 3
+            else:
+                E = [child_interp_1d(nH, nh, b) for b in bits]
+            blk = np.kron(E[2], np.kron(E[1], E[0]))
+            r = np.arange(fine.dof_off[c], fine.dof_off[c + 1])
+            q = np.arange(coarse.dof_off[H], coarse.dof_off[H + 1])
+            rr, qq = np.meshgrid(r, q, indexing='ij')
+            rows.append(rr.ravel()); cols.append(qq.ravel()); vals.append(blk.ravel())
+    P = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(fine.n_dofs, coarse.n_dofs)).tocsr()
+    P.eliminate_zeros()
+    return P
+
+
+def cgeigs(A, x, b, n_iter):
+    """Alg. 5: n_iter CG steps from x with the Gershgorin bound of the
+    Lanczos tridiagonal.  Returns (lambda_max, x)."""
+    x = x.copy()
+    r = b - A @ x
+    p = r.copy()
+    rr = r @ r
+    lam = 0.0
+    a_prev = b_prev = None
+    for k in range(n_iter):
+        Ap = A @ p
+        pAp = p @ Ap
+        if not (pAp > 0.0) or rr == 0.0:
+            break
+        a = rr / pAp
+        x += a * p
+        r -= a * Ap
+        rr_new = r @ r
+        beta = rr_new / rr
+        rr = rr_new
+        p = r + beta * p
+        diag = 1.0 / a
+        left = 0.0
+        if a_prev is not None:
+            diag += b_prev / a_prev
+            left = np.sqrt(b_prev) / a_prev
+        right = np.sqrt(beta) / a
+        lam = max(lam, diag + left + right)
+        a_prev, b_prev = a, beta
+    return lam, x
+
+
+def chebyshev(A, x, b, lam_max, Lam, n_iter):
+    """Chebyshev steps of Alg. 4 on [lam_max / Lam, lam_max]."""
+    x = x.copy()
+    if not (lam_max > 0.0):
+        return x
+    lmin = lam_max / Lam
+    c = 0.5 * (lam_max - lmin)
+    d = 0.5 * (lam_max + lmin)
+    p = np.zeros_like(x)
+    alpha = 0.0
+    for k in range(1, n_iter + 1):
+        r = b - A @ x
+        if k == 1:
+            alpha = 1.0 / d
+        elif k == 2:
+            alpha = 2.0 * d / (2.0 * d * d - c * c)
+        else:
+            alpha = 1.0 / (d - alpha * c * c / 4.0)
+        beta = alpha * d - 1.0
+        p = alpha * r + beta * p
+        x = x + p
+    return x
+
+
+def smoother(A, x, b, n_eigs=15, n_cheb=15, Lam=20.0):
+    """Alg. 4: CGEIGS then Chebyshev from the CG-updated x."""
+    lam, x = cgeigs(A, x, b, n_eigs)
+    return chebyshev(A, x, b, lam, Lam, n_cheb), lam
+
+
+class Hierarchy:
+    """Level operators J_l and prolongations for the V-cycle of Alg. 3."""
+
+    def __init__(self, mesh, C=10.0, coef=None, extra=0):
+        from . import sipg
+        self.meshes, self.groups = hierarchy(mesh)
+        self.P = [prolongation(self.meshes[l + 1], self.meshes[l], self.groups[l])
+                  for l in range(len(self.meshes) - 1)]
+        self.L = [sipg.assemble(m, C, extra) for m in self.meshes]
+        self.J = list(self.L)
+        if coef is not None:
+            O = sipg.assemble(mesh, C, extra, coef) - self.L[-1]
+            self.O = [None] * len(self.meshes)
+            self.O[-1] = O
+            for l in range(len(self.meshes) - 2, -1, -1):
+                self.O[l] = (self.P[l].T @ self.O[l + 1] @ self.P[l]).tocsr()
+            self.J = [self.L[l] + self.O[l] for l in range(len(self.meshes))]
+        self._chol = None
+
+    @property
+    def n_levels(self):
+        return len(self.meshes)
+
+    def coarse_cholesky(self, f):
+        if self._chol is None:
+            self._chol = sla.cho_factor(self.J[0].toarray())
+        return sla.cho_solve(self._chol, f)
+
+    def vcycle(self, f, n_eigs=15, n_cheb=15, Lam=20.0, coarse='smoother'):
+        """Alg. 3 with the level meshes fixed in advance."""
+        Lt = self.n_levels - 1
+        fs = [None] * (Lt + 1)
+        vs = [None] * (Lt + 1)
+        fs[Lt] = f
+        for l in range(Lt, 0, -1):
+            v = np.zeros_like(fs[l])
+            v, _ = smoother(self.J[l], v, fs[l], n_eigs, n_cheb, Lam)
+            vs[l] = v
+            fs[l - 1] = self.P[l - 1].T @ (fs[l] - self.J[l] @ v)
+        if coarse == 'cholesky':
+            vs[0] = self.coarse_cholesky(fs[0])
+        else:
+            vs[0], _ = smoother(self.J[0], np.zeros_like(fs[0]), fs[0], n_eigs, n_cheb, Lam)
+        for l in range(1, Lt + 1):
+            v = self.P[l - 1] @ vs[l - 1] + vs[l]
+            vs[l], _ = smoother(self.J[l], v, fs[l], n_eigs, n_cheb, Lam)
+        return vs[Lt]

@@ -1,0 +1,98 @@
+"""Puncture initial data (Sec. III.D, eqs. Two_Punctures_PDE, Two_Punctures_Aij)
+and Newton-Raphson (Alg. 1) (oracle; test infrastructure only).
+
+With 1/alpha = sum_I m_I / (2 r_I) and psi = 1 + 1/alpha + u the equation
+-Lap u = (1/8) A_ij A^ij psi^-7 becomes
+    R(u) = -Lap u - beta (1 + alpha (1 + u))^-7 = 0,  beta = alpha^7 A_ij A^ij / 8,
+and its linearisation J_R du = -Lap du + 7 alpha beta (1 + alpha (1 + u))^-8 du
+(eq. temp-F form: the zeroth-order coefficient f(u_0)).  Nonlinear terms are
+evaluated at the volume GL points after interpolating u there (Sec. III.B).
+
+Readings:
+ * Zero spin: A_ij = sum_I 3 / (2 r_I^2) [P_i n_j + P_j n_i - (delta_ij - n_i n_j) P.n]
+   (the printed spin term is garbled; the workloads use S = 0).
+ * Outer boundary: u = 0 Dirichlet on the box (u -> 0 at infinity).
+ * Newton loop: while k < N_NK and ||R(u_k)|| >= tol_NK (Alg. 1 joins the two
+   tests with "or").
+
+Pins: single-puncture closed form A_ij A^ij = 9 / (2 r^4) (|P|^2 + 2 (P.n)^2),
+J_R v against a central finite difference of R, quadratic Newton
+convergence (tests/test_oracle_puncture.py).
+"""
+import numpy as np
+
+from . import tables, sipg
+
+
+def alpha_beta(x, punctures):
+    """alpha and beta at points x (P, 3); punctures: list of (m, c(3), P(3))."""
+    x = np.asarray(x, dtype=np.float64)
+    inv_alpha = np.zeros(len(x))
+    A = np.zeros((len(x), 3, 3))
+    I3 = np.eye(3)
+    for (m, c, P) in punctures:
+        dx = x - np.asarray(c, dtype=np.float64)
+        r = np.linalg.norm(dx, axis=1)
+        nvec = dx / r[:, None]
+        P = np.asarray(P, dtype=np.float64)
+        Pn = nvec @ P
+        term = (np.einsum('i,pj->pij', P, nvec) + np.einsum('pi,j->pij', nvec, P)
+                - (I3[None] - np.einsum('pi,pj->pij', nvec, nvec)) * Pn[:, None, None])
+        A += (1.5 / r ** 2)[:, None, None] * term
+        inv_alpha += m / (2.0 * r)
+    AA = np.einsum('pij,pij->p', A, A)
+    alpha = 1.0 / inv_alpha
+    beta = alpha ** 7 * AA / 8.0
+    return alpha, beta, AA
+
+
+class PunctureProblem:
+    def __init__(self, mesh, punctures, C=10.0):
+        self.mesh = mesh
+        self.C = C
+        self.L = sipg.assemble(mesh, C)
+        self.data = []
+        for e in range(mesh.n_elems):
+            n = int(mesh.n[e])
+            xl, _ = tables.lgl_nodes_weights(n)
+            xi, w, J, detJ, Jinv = sipg.volume_geometry(mesh, e)
+            Psi, _ = tables.basis3d(xl, xi)
+            x = mesh.position_at(e, xi)
+            al, be, _ = alpha_beta(x, punctures)
+            self.data.append((Psi, w * detJ, al, be))
+
+    def _gl(self, u):
+        off = self.mesh.dof_off
+        for e, (Psi, wd, al, be) in enumerate(self.data):
+            yield e, Psi, wd, al, be, Psi @ u[off[e]:off[e + 1]]
+
+    def residual(self, u):
+        """R_alpha = (L u)_alpha - int beta (1 + alpha (1 + u))^-7 psi_alpha."""
+        R = self.L @ u
+        off = self.mesh.dof_off
+        for e, Psi, wd, al, be, ug in self._gl(u):
+            R[off[e]:off[e + 1]] -= Psi.T @ (wd * be * (1.0 + al * (1.0 + ug)) ** -7)
+        return R
+
+    def jacobian_coef(self, u):
+        """Per element: f(u) = 7 alpha beta (1 + alpha (1 + u))^-8 at GL points."""
+        return [7.0 * al * be * (1.0 + al * (1.0 + ug)) ** -8 for e, Psi, wd, al, be, ug in self._gl(u)]
+
+    def jacobian(self, u):
+        return sipg.assemble(self.mesh, self.C, coef=self.jacobian_coef(u))
+
+
+def newton(prob, u0, lsolve, tol=1e-10, max_iter=20):
+    """Alg. 1 with linear solver lsolve(J_coef, rhs) -> du."""
+    u = u0.copy()
+    hist = []
+    k = 0
+    while k < max_iter:
+        R = prob.residual(u)
+        hist.append(np.linalg.norm(R))
+        if hist[-1] < tol:
+            break
+        du = lsolve(prob.jacobian_coef(u), -R)
+        u = u + du
+        k += 1
+    return u, k, hist

@@ -1,0 +1,131 @@
+"""Pins for the oracle's multigrid pieces (Algs. 2-5, eqs. psi-interpolation,
+temp-G, operator_oh)."""
+import numpy as np
+import pytest
+
+from oracle import krylov, multigrid, sipg, tables
+from oracle.mesh import Mesh
+from paper_1907_01572_gb300 import inputs
+
+
+def test_chebyshev_error_polynomial():
+    """Alg. 4 (with p <- alpha r + beta p): after k steps from x = 0 each
+    eigencomponent of the error is T_k((d - lam)/c) / T_k(d/c) times the initial one."""
+    rng = np.random.default_rng(0)
+    lmax, Lam = 4.0, 20.0
+    lam = np.sort(rng.uniform(0.05, lmax, 40))
+    A = np.diag(lam)
+    xs = rng.standard_normal(40)
+    b = A @ xs
+    lmin = lmax / Lam
+    c, d = (lmax - lmin) / 2, (lmax + lmin) / 2
+    for k in (1, 2, 3, 7, 15):
+        x = multigrid.chebyshev(A, np.zeros(40), b, lmax, Lam, k)
+        Tk = np.polynomial.chebyshev.Chebyshev.basis(k)
+        expect = Tk((d - lam) / c) / Tk(d / c) * xs
+        assert np.allclose(xs - x, expect, atol=1e-10), k
+
+
+def test_chebyshev_printed_sign_is_not_chebyshev():
+    """The printed update p <- alpha r - beta p does not give the Chebyshev
+    error polynomial (pins the reading)."""
+    rng = np.random.default_rng(1)
+    lam = np.sort(rng.uniform(0.2, 4.0, 30))
+    A = np.diag(lam)
+    xs = rng.standard_normal(30)
+    b = A @ xs
+    lmax, Lam = 4.0, 20.0
+    lmin = lmax / Lam
+    c, d = (lmax - lmin) / 2, (lmax + lmin) / 2
+    x, p, alpha = np.zeros(30), np.zeros(30), 0.0
+    for k in range(1, 4):
+        r = b - A @ x
+        alpha = 1 / d if k == 1 else (2 * d / (2 * d * d - c * c) if k == 2 else 1 / (d - alpha * c * c / 4))
+        beta = alpha * d - 1
+        p = alpha * r - beta * p
+        x = x + p
+    T3 = np.polynomial.chebyshev.Chebyshev.basis(3)
+    assert not np.allclose(xs - x, T3((d - lam) / c) / T3(d / c) * xs, atol=1e-6)
+
+
+def test_cgeigs_cg_iterates_and_bound():
+    m = Mesh((-1, -1, -1), (1, 1, 1), inputs.uniform_leaves(1), [3] * 8)
+    A = sipg.assemble(m, 10.0)
+    rng = np.random.default_rng(2)
+    b = rng.standard_normal(m.n_dofs)
+    lam, x = multigrid.cgeigs(A, np.zeros(m.n_dofs), b, 10)
+    # textbook CG (written independently)
+    xx, r = np.zeros(m.n_dofs), b.copy()
+    p = r.copy()
+    for _ in range(10):
+        Ap = A @ p
+        a = (r @ r) / (p @ Ap)
+        xx = xx + a * p
+        rn = r - a * Ap
+        p = rn + (rn @ rn) / (r @ r) * p
+        r = rn
+    assert np.allclose(x, xx, rtol=1e-10, atol=1e-12)
+    lmax = np.linalg.eigvalsh(A.toarray()).max()
+    assert lam >= 0.8 * lmax
+    lam50, _ = multigrid.cgeigs(A, np.zeros(m.n_dofs), b, 50)
+    assert lam50 >= lmax * (1 - 1e-8)
+
+
+def test_prolongation_exact_and_restriction_transpose():
+    d = inputs.sweep_mesh(level=2, seed=0)
+    a, k = inputs.oracle_mesh_args(d)
+    fine = Mesh(*a, **k)
+    coarse, groups = multigrid.coarsen(fine)
+    P = multigrid.prolongation(fine, coarse, groups)
+    # prolonging the interpolant of a polynomial of degree <= min p (= 2) reproduces it
+    f = lambda x: 1 + x[:, 0] - 2 * x[:, 1] * x[:, 2] + 0.5 * x[:, 0] ** 2
+    # on the unwarped mesh, nodal interpolation is exact for this quadratic
+    fine0 = Mesh(fine.lo, fine.hi, fine.leaves, fine.p)
+    coarse0 = Mesh(coarse.lo, coarse.hi, coarse.leaves, coarse.p)
+    P0 = multigrid.prolongation(fine0, coarse0, groups)
+    assert np.abs(P0 @ sipg.interpolate(coarse0, f) - sipg.interpolate(fine0, f)).max() < 1e-13
+    # coarse p is the minimum of the children and all families are 2:1 balanced
+    for H, grp in enumerate(groups):
+        assert coarse.p[H] == min(fine.p[c] for c, _ in grp)
+    assert P.shape == (fine.n_dofs, coarse.n_dofs)
+
+
+def test_hierarchy_levels_and_balance():
+    d = inputs.sweep_mesh(level=2, seed=0)
+    a, k = inputs.oracle_mesh_args(d)
+    meshes, groups = multigrid.hierarchy(Mesh(*a, **k))
+    assert [m.n_elems for m in meshes] == [1, 8, 15, 120]
+    # every level is a valid 2:1 mesh (Mesh construction raises otherwise)
+    for m in meshes:
+        assert m.n_dofs > 0
+
+
+def test_galerkin_zeroth_order_identity():
+    """O^H = I^T O^h I equals the coarse mass matrix assembled with the fine
+    level's quadrature (eq. temp-H) -- checked through bilinear forms."""
+    lv = inputs.uniform_leaves(1)
+    fine = Mesh((-1, -1, -1), (1, 1, 1), lv, [2] * 8)
+    coarse, groups = multigrid.coarsen(fine)
+    P = multigrid.prolongation(fine, coarse, groups)
+    coef = [np.full((fine.n[e]) ** 3, 1.5) for e in range(8)]
+    Oh = sipg.assemble(fine, 10.0, coef=coef) - sipg.assemble(fine, 10.0)
+    OH = (P.T @ Oh @ P).toarray()
+    # coarse mass with constant coefficient 1.5 on the p=2 coarse element is exact
+    Mc = sipg.element_mass(coarse, 0, np.full(125, 1.5), extra=2)
+    assert np.abs(OH - Mc).max() < 1e-12 * np.abs(Mc).max()
+
+
+def test_fcg_identity_is_cg_and_mg_solve():
+    m = Mesh((-1, -1, -1), (1, 1, 1), inputs.uniform_leaves(2), [3] * 64)
+    H = multigrid.Hierarchy(m)
+    u = lambda x: np.sin(np.pi * x[:, 0]) * np.sin(np.pi * x[:, 1]) * np.sin(np.pi * x[:, 2])
+    F = sipg.rhs(m, lambda x: 3 * np.pi ** 2 * u(x), u)
+    x, it, hist = krylov.fcg(H.J[-1], F, precond=lambda r: H.vcycle(r), tol=1e-10)
+    assert hist[-1] < 1e-10 and it <= 12
+    r = F - H.J[-1] @ x
+    assert np.linalg.norm(r) / np.linalg.norm(F) < 1e-9
+    x2, it2, _ = krylov.fcg(H.J[-1], F, precond=lambda r: H.vcycle(r, coarse='cholesky'), tol=1e-10)
+    assert it2 <= it + 1
+    # no preconditioner: FCG(1) iterates are CG's, far more iterations
+    _, it3, _ = krylov.fcg(H.J[-1], F, tol=1e-10, max_iter=1000)
+    assert it3 > 5 * it
