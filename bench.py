@@ -1,0 +1,308 @@
+"""Benchmark: matrix-free SIPG operator apply on the curved, 2:1 h-refined,
+mixed-degree 32^3 sweep mesh (61,440 elements, p drawn from {2..7}, ~1.32e7
+DOFs), plus the Poisson solve of the 4x4x4, p = 3 problem at 1e-10 relative
+residual (solves/s, p50/p99).
+
+One step = one operator apply y = L x over the whole mesh (all degree
+buckets) in FP32; the FP64 apply and the solve are reported beside it.
+Prints ONE JSON line.  Multi-GPU: independent replicas (no collective on the
+data path), value = DOFs applied by all ranks / max time.
+
+--impl reference times the oracle (plain FP64 numpy, dense per-element
+blocks) on the host cores on a bounded element sample of the same workload.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+HBM_FALLBACK = 6800.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline_sample(n_elems_sample, seed=0):
+    """Times the oracle's dense-local apply on a sample of the sweep mesh's
+    elements in a single-threaded subprocess; returns (GDOF/s, dofs, seconds)."""
+    code = r"""
+import os, sys, time, json
+sys.path.insert(0, %r)
+import numpy as np
+from paper_1907_01572_gb300 import inputs
+from oracle.mesh import Mesh
+from oracle import sipg
+desc = inputs.sweep_mesh(level=5, seed=0)
+a, k = inputs.oracle_mesh_args(desc)
+m = Mesh(*a, **k)
+rng = np.random.default_rng(%d)
+els = rng.choice(m.n_elems, size=%d, replace=False)
+x = inputs.random_vector(m.n_dofs, seed=1)
+t = time.perf_counter()
+out = sipg.apply_local(m, x, 10.0, elems=[int(e) for e in els])
+dt = time.perf_counter() - t
+dofs = int(sum((m.p[e] + 1) ** 3 for e in els))
+print(json.dumps({"dofs": dofs, "seconds": dt}))
+""" % (ROOT, seed, n_elems_sample)
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d["dofs"] / d["seconds"] / 1e9, d["dofs"], d["seconds"]
+
+
+WORKLOAD = "operator-apply sweep: 32^3 hex on [-1,1]^3, octant x,y,z<0 h-refined 2:1 (61440 elems), " \
+           "p~U{2..7} seed 0, sine-warped isoparametric geometry, x~N(0,1) seed 1"
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    vals, secs = [], []
+    for s in range(args.warmup + args.steps):
+        g, dofs, dt = cpu_baseline_sample(16, seed=100 + s)
+        if s >= args.warmup:
+            vals.append(g)
+            secs.append(dt)
+    v = sum(vals) / len(vals)
+    line = {"impl": "reference", "metric": "DG apply GDOF/s", "value": v, "unit": "GDOF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": v, "unit": "GDOF/s", "cores": 1, "kind": "oracle",
+                             "sample": "16 random elements per step, dense-local FP64 apply incl. their mortars"},
+            "e2e": {"value": v, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours")
+    ap.add_argument("--level", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solve", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    # CPU baseline first (own process, before any heavy GPU work)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        g, dofs, dt = cpu_baseline_sample(24, seed=0)
+        cpu = {"value": g, "unit": "GDOF/s", "cores": 1, "kind": "oracle",
+               "sample": "24 random elements (%d DOFs, %.1f s) of the same mesh, dense-local FP64 apply "
+                         "incl. their mortars, single thread" % (dofs, dt)}
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1907_01572_gb300 import dgell, inputs
+
+    stream = torch.cuda.current_stream()
+    desc = inputs.sweep_mesh(level=args.level, seed=0)
+    ctx = dgell.Context(desc)
+    info = ctx.level_info()
+    N = info["n_dofs"]
+    x64 = torch.tensor(inputs.random_vector(N, seed=1), device="cuda")
+    x32 = x64.float()
+    y32 = torch.empty_like(x32)
+    y64 = torch.empty_like(x64)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        return e0.elapsed_time(e1) / steps  # ms per step
+
+    hbm, peak_kind = peaks()
+    launches0 = ctx.launch_count()
+    with Clocks(local) as clk:
+        ms32 = timed(lambda: ctx.apply(x32, y32), args.steps, args.warmup)
+    launches = (ctx.launch_count() - launches0) * args.steps // (args.steps + args.warmup)
+    ms64 = timed(lambda: ctx.apply(x64, y64), max(3, args.steps // 4), args.warmup)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the region
+    hx = x32.cpu().pin_memory()
+    hy = torch.empty_like(hx).pin_memory()
+    dx = torch.empty_like(x32)
+    dy = torch.empty_like(x32)
+
+    def e2e_step():
+        dx.copy_(hx, non_blocking=True)
+        ctx.apply(dx, dy)
+        hy.copy_(dy, non_blocking=True)
+
+    ms_e2e = timed(e2e_step, max(3, args.steps // 2), 2)
+
+    tms = torch.tensor([ms32, ms64, ms_e2e], device="cuda")
+    if dist:
+        dist.all_reduce(tms, op=dist.ReduceOp.MAX)
+    ms32, ms64, ms_e2e = [float(v) for v in tms.cpu()]
+    total_dofs = N * world
+    g32 = total_dofs / (ms32 * 1e-3) / 1e9
+    g64 = total_dofs / (ms64 * 1e-3) / 1e9
+    ge2e = total_dofs / (ms_e2e * 1e-3) / 1e9
+
+    # algorithmic bytes per DOF: x + y + 3 coordinates per LGL node (curved isoparametric geometry)
+    b32 = 4 + 4 + 12
+    b64 = 8 + 8 + 24
+    ach32 = N * b32 / (ms32 * 1e-3) / 1e9
+    ach64 = N * b64 / (ms64 * 1e-3) / 1e9
+
+    solve = None
+    if not args.no_solve and rank == 0:
+        solve = solve_bench(dgell, inputs, torch)
+
+    if rank == 0:
+        line = {
+            "metric": "DG apply GDOF/s", "value": g32, "unit": "GDOF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_dofs": N, "n_elems": info["n_elems"], "levels": info["n_levels"],
+                       "l2": "inputs larger than L2 (x, y, metric terms ~0.6 GB)", "parallelism": "replicas"},
+            "roofline": {"bound": "hbm", "achieved": ach32, "peak": hbm, "unit": "GB/s", "frac": ach32 / hbm,
+                         "traffic": None, "peak_kind": peak_kind,
+                         "bytes_per_dof": b32, "kernel": "apply_kernel (all degree buckets, one apply)"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": ge2e, "unit": "GDOF/s", "h2d_bytes_per_step": N * 4, "d2h_bytes_per_step": N * 4},
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+            "fp64": {"value": g64, "unit": "GDOF/s", "ms_per_step": ms64, "achieved_gbs": ach64,
+                     "bytes_per_dof": b64},
+            "solve": solve,
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def solve_bench(dgell, inputs, torch, n_solves=8):
+    """Poisson -Lap u = 3 pi^2 sin sin sin on 4^3 elements, p = 3, MG-FCG to 1e-10."""
+    import numpy as np
+    desc = inputs.config1_mesh()
+    ctx = dgell.Context(desc)
+    xyz, bxyz = ctx.quadrature_points()
+    g = 3 * np.pi ** 2 * torch.sin(np.pi * xyz[0]) * torch.sin(np.pi * xyz[1]) * torch.sin(np.pi * xyz[2])
+    N = ctx.level_info()["n_dofs"]
+    F = torch.empty(N, dtype=torch.float64, device="cuda")
+    ctx.rhs(g.contiguous(), None, F)
+    out = {}
+    for name, prec in (("fp64", dgell.DG_FP64), ("mixed_fp32_vcycle", dgell.DG_FP32)):
+        lat, its, res = [], [], []
+        for s in range(n_solves + 2):
+            x = torch.zeros_like(F)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            st = ctx.solve(F, x, tol=1e-10, max_iter=100, mg_prec=prec)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t
+            if s >= 2:
+                lat.append(dt)
+                its.append(st["iterations"])
+                res.append(st["rel_residual"])
+        lat.sort()
+        out[name] = {"solves_per_s": len(lat) / sum(lat), "p50_ms": 1e3 * lat[len(lat) // 2],
+                     "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))], "iterations": its[-1],
+                     "max_rel_residual": max(res)}
+    ctx.close()
+    out["workload"] = "Poisson 4x4x4 affine hex, p=3 (4096 DOFs), manufactured sin solution, tol 1e-10"
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

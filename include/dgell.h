@@ -1,0 +1,242 @@
+/*
+ * dgell.h -- C ABI of the GB300 (sm_103a) matrix-free hp-DG elliptic solver.
+ *
+ * Method: symmetric interior penalty DG (SIPG) discretisation of
+ *     -Lap u + f u = g  in Omega,   u = g_D on the Dirichlet boundary,
+ * on h- and p-non-conforming hexahedral meshes (Vincent, Pfeiffer & Fischer,
+ * arXiv:1907.01572, Sec. II.A-II.D), with a Chebyshev/CG-eigenvalue smoothed
+ * multigrid V-cycle (Sec. II.E, Algs. 3-5) preconditioning flexible CG
+ * (Alg. 2), and Newton-Raphson (Alg. 1) for the puncture equation (Sec. III.D).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every call returns an int status: DG_OK (0) or one of DG_ERR_*.
+ *    dg_last_error() returns a thread-local message for the last failure.
+ *  - Vectors are element-blocked: element e of a level owns the contiguous
+ *    block [dof_off[e], dof_off[e] + (p_e+1)^3); inside the block the LGL node
+ *    (a, b, c) (a along x fastest) is at a + n b + n^2 c, n = p_e + 1.
+ *    Element order on the finest level is the order of the mesh description;
+ *    on coarser levels it is the order of each coarse element's first
+ *    appearance while scanning the finer level (dg_level_leaves reports it).
+ *  - Levels follow the paper: 0 is the coarsest, L = n_levels - 1 the finest
+ *    (the input mesh).  level = -1 means the finest.
+ *  - "device" pointers are CUDA global-memory pointers on the context's
+ *    device; they are owned by the caller unless stated otherwise and must
+ *    stay valid until the work queued on the context's stream has finished.
+ *    All device work is queued on the stream given at context creation.
+ *  - Precision codes: DG_FP64 (double vectors, double arithmetic),
+ *    DG_FP32 (float vectors, float arithmetic); DG_BF16 is reserved.
+ */
+#ifndef DGELL_H
+#define DGELL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DGELL_VERSION 100
+
+enum {
+    DG_OK = 0,
+    DG_ERR_INVALID = 1,        /* bad argument, malformed mesh (not 2:1, p out of range, ...) */
+    DG_ERR_OOM = 2,            /* device allocation failed */
+    DG_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+    DG_ERR_NOT_CONVERGED = 4,  /* iteration cap reached; statistics are filled */
+    DG_ERR_BREAKDOWN = 5,      /* non-finite or non-positive Krylov scalar */
+    DG_ERR_UNSUPPORTED = 6     /* valid request this build does not implement */
+};
+
+typedef enum { DG_FP64 = 0, DG_FP32 = 1, DG_BF16 = 2 } dg_prec;
+
+typedef enum {
+    DG_MAP_AFFINE = 0,      /* block map = identity on the box [lo, hi]^3 */
+    DG_MAP_SINE_WARP = 1    /* x_i += a sin(2 pi k_i x_i) sin(2 pi k_{i+1} x_{i+1}), cyclic i */
+} dg_map_kind;
+
+/* Mesh description (Sec. II.A.1: one macro-element, the box [lo, hi]^3,
+ * refined as an octree).  All arrays are HOST memory; dg_ctx_create copies
+ * them.  leaves: n_elems x 4 ints (level, ix, iy, iz), a level-l leaf has
+ * width (hi - lo) / 2^l; leaves must tile the box with at most 2:1 level
+ * difference across faces.  p: n_elems degrees in 1..8.  Geometry is
+ * isoparametric: the block map is sampled at each element's own LGL nodes. */
+typedef struct {
+    double lo[3];
+    double hi[3];
+    int map_kind;          /* dg_map_kind */
+    double warp_amp;       /* a of DG_MAP_SINE_WARP */
+    int warp_k[3];         /* k_i of DG_MAP_SINE_WARP */
+    int n_elems;
+    const int* leaves;     /* host, n_elems * 4 */
+    const int* p;          /* host, n_elems */
+} dg_mesh_desc;
+
+/* Discretisation options.  penalty_c is C of eq. (penaltyparameter),
+ * sigma = C p_m^2 / h_m; <= 0 selects the default 10. */
+typedef struct {
+    double penalty_c;
+    int reserved[4];
+} dg_disc_opts;
+
+typedef struct dg_ctx dg_ctx;
+
+typedef struct {
+    int n_levels;
+    int n_elems;           /* of the requested level */
+    int64_t n_dofs;        /* of the requested level */
+    int64_t n_vol_qp;      /* volume GL points of the level (sum of (p+1)^3) */
+    int64_t n_bnd_qp;      /* Dirichlet-boundary mortar GL points of the level */
+    int n_mortars;
+    int max_p;
+    size_t device_bytes;   /* device memory held by the whole context */
+} dg_level_info;
+
+int dg_version(void);
+const char* dg_last_error(void);
+
+/* Builds the mesh hierarchy (Sec. II.E.3: surrogate coarsening + 2:1
+ * rebalancing, coarse degree = min over children), mortar tables, the 1-D
+ * operator tables and all geometry (eqs. Jacobian, Surface-Jacobian, the
+ * normal, eq. penaltyparameter) on the device.  stream: a cudaStream_t
+ * (NULL = legacy default stream).  Synchronises the stream before return. */
+int dg_ctx_create(const dg_mesh_desc* mesh, const dg_disc_opts* opts, void* stream, dg_ctx** out);
+void dg_ctx_destroy(dg_ctx* ctx);
+
+/* Device bytes dg_ctx_create would hold for this mesh (admission control);
+ * host-only, no device work. */
+int dg_ctx_footprint(const dg_mesh_desc* mesh, const dg_disc_opts* opts, size_t* bytes);
+
+int dg_level_info_get(dg_ctx* ctx, int level, dg_level_info* info);
+
+/* Host copies of a level's leaves (n_elems x 4), degrees (n_elems) and
+ * element DOF offsets (n_elems + 1).  Any pointer may be NULL. */
+int dg_level_leaves(dg_ctx* ctx, int level, int* leaves, int* p, int64_t* dof_off);
+
+/* Physical coordinates (device, double, 3 x n) of the level's volume GL
+ * points (SoA: x[0..n), y[n..2n), z[2n..3n)), element by element, point
+ * (i, j, k) of element e at vol_qp_off[e] + i + q j + q^2 k, q = p_e + 1.
+ * Same for the Dirichlet-boundary mortar points (bnd).  Either may be NULL. */
+int dg_quadrature_points(dg_ctx* ctx, int level, double* vol_xyz, double* bnd_xyz);
+
+/* y = L x: the SIPG operator of eq. (lh2) (stiffness + consistency +
+ * symmetry + penalty on interior and Dirichlet mortars, plus the zeroth-order
+ * term int f u v when one was set with dg_set_zeroth_order), applied
+ * matrix-free on level `level` (Sec. II.A.5, eq. harald-stiff; mortar
+ * integrals with hp mortar projection, mortar figure).  x, y: device
+ * vectors of the level's n_dofs in precision prec (double for DG_FP64,
+ * float for DG_FP32); x and y must not overlap.  Asynchronous. */
+int dg_apply(dg_ctx* ctx, int level, int prec, const void* x, void* y);
+
+/* Right-hand side F_h of eq. (equationFh2) on the finest level:
+ * F = int g v - int_{Gamma_D} g_D n.grad v + int_{Gamma_D} sigma g_D v.
+ * g_qp: device double values of g at the finest level's volume GL points
+ * (dg_quadrature_points order) or NULL for g = 0; gD_qp: device double values
+ * of g_D at the boundary mortar points or NULL for g_D = 0.  F: device
+ * double, n_dofs.  Asynchronous. */
+int dg_rhs(dg_ctx* ctx, const double* g_qp, const double* gD_qp, double* F);
+
+/* Chebyshev smoother (Alg. 4) with CG spectral bound (Alg. 5).  Smooths
+ * J x = b on `level` in place: n_eigs CG steps (which also update x) give
+ * lambda_max by Gershgorin on the Lanczos tridiagonal; then n_cheb Chebyshev
+ * steps on [lambda_max / Lambda, lambda_max].  b, x: device vectors of the
+ * level in precision prec.  lambda_max_out: host pointer or NULL (forces a
+ * stream synchronisation when given). */
+typedef struct {
+    int n_eigs;        /* N_iter,eigs; <= 0 -> 15 */
+    int n_cheb;        /* N_iter,Cheb; <= 0 -> 15 */
+    double Lambda;     /* lambda_max / lambda_min; <= 0 -> 20 */
+} dg_cheb_opts;
+
+int dg_smooth(dg_ctx* ctx, int level, int prec, const void* b, void* x,
+              const dg_cheb_opts* opts, double* lambda_max_out);
+
+/* Multigrid V-cycle (Alg. 3) as a preconditioner: v = VCYCLE(f) on the
+ * finest level, starting from v = 0 on every level, pre- and post-smoothing
+ * with dg_smooth's smoother, restriction = transpose of the prolongation
+ * (eq. temp-G), coarse level: smoother (coarse = 0) or exact Cholesky
+ * solve (coarse = 1).  f, v: device vectors of the finest level in prec. */
+typedef struct {
+    dg_cheb_opts cheb;
+    int coarse;        /* 0: smoother on level 0 (paper), 1: dense Cholesky */
+} dg_mg_opts;
+
+int dg_vcycle(dg_ctx* ctx, int prec, const void* f, void* v, const dg_mg_opts* opts);
+
+/* Flexible CG (Alg. 2) on the finest level, FP64 vectors, preconditioned by
+ * the V-cycle in precision opts->mg_prec (DG_FP64: the plain FP64 form;
+ * DG_FP32: FP32 V-cycle inside the FP64 Krylov loop, i.e. mixed precision).
+ * b, x: device double, n_dofs; x holds the initial guess on entry.  Stops
+ * when ||b - J x||_2 <= tol ||b||_2 (recursive residual, confirmed with a
+ * true FP64 residual at exit) or after max_iter iterations. */
+typedef struct {
+    double tol;        /* relative residual target; <= 0 -> 1e-10 */
+    int max_iter;      /* N_iter,FCG; <= 0 -> 100 */
+    int mg_prec;       /* precision of the V-cycle: DG_FP64 or DG_FP32 */
+    int use_mg;        /* 0: no preconditioner (plain CG iterates) */
+    dg_mg_opts mg;
+} dg_solver_opts;
+
+typedef struct {
+    int iterations;
+    double rel_residual;       /* true ||b - J x|| / ||b|| at exit */
+    double rel_residual_rec;   /* recursive residual at exit */
+    double seconds;            /* host wall time of the call */
+    int status;
+} dg_solve_stats;
+
+int dg_solve(dg_ctx* ctx, const double* b, double* x, const dg_solver_opts* opts, dg_solve_stats* stats);
+
+/* Zeroth-order term int f u v of eq. (lh2) on the finest level:
+ * coef_qp: device double values of f at the finest level's volume GL
+ * points (NULL clears the term).  Coarse levels get the Galerkin form
+ * O^H = I^T O^h I of eq. (operator_oh) as dense per-element blocks. */
+int dg_set_zeroth_order(dg_ctx* ctx, const double* coef_qp);
+
+/* Puncture initial data (Sec. III.D, zero spin):
+ * R(u) = -Lap u - beta (1 + alpha (1 + u))^-7, u = 0 on the box boundary,
+ * 1/alpha = sum m_I / (2 r_I), beta = alpha^7 A_ij A^ij / 8. */
+typedef struct {
+    int n;                 /* number of punctures, <= 16 */
+    double m[16];
+    double c[16][3];       /* positions */
+    double P[16][3];       /* linear momenta */
+} dg_puncture_params;
+
+/* Evaluates alpha, beta at the finest level's volume GL points and keeps
+ * them in the context for dg_newton_*. */
+int dg_puncture_setup(dg_ctx* ctx, const dg_puncture_params* params);
+
+/* Weak residual R(u) (device double, n_dofs) of the puncture equation. */
+int dg_puncture_residual(dg_ctx* ctx, const double* u, double* R);
+
+/* One Newton step (Alg. 1): sets the Jacobian's zeroth-order term
+ * 7 alpha beta (1 + alpha (1 + u))^-8, solves J du = -R(u) with dg_solve and
+ * updates u += du.  u: device double, n_dofs.  residual_norm_out: host,
+ * ||R(u)||_2 before the step (may be NULL). */
+int dg_newton_step(dg_ctx* ctx, double* u, const dg_solver_opts* opts, dg_solve_stats* stats,
+                   double* residual_norm_out);
+
+/* Newton-Raphson: at most max_newton steps until ||R(u)||_2 < tol_newton. */
+int dg_newton_solve(dg_ctx* ctx, double* u, double tol_newton, int max_newton,
+                    const dg_solver_opts* opts, int* steps_out, double* residual_norm_out);
+
+/* Inter-level transfer between level `coarse_level` (H) and coarse_level + 1
+ * (h) (Sec. II.E.6): direction 0 = prolongation, out_h += I_h^H in_H
+ * (eq. psi-interpolation); direction 1 = restriction of a weak residual,
+ * out_H = (I_h^H)^T in_h (eq. temp-G).  Device vectors in prec. */
+int dg_transfer(dg_ctx* ctx, int coarse_level, int prec, int direction, const void* in, void* out);
+
+/* Vector helpers used by the binding's tests and the bench (device memory,
+ * on the context stream): precision conversion double <-> float. */
+int dg_convert(dg_ctx* ctx, int64_t n, int src_prec, const void* src, int dst_prec, void* dst);
+
+/* Kernel launches issued by the library since context creation (counter of
+ * this library's own kernels). */
+int64_t dg_launch_count(dg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGELL_H */

@@ -1,0 +1,69 @@
+// Vector kernels, deterministic reductions and the device-resident scalar
+// recurrences of CG (Alg. 5), Chebyshev (Alg. 4) and flexible CG (Alg. 2).
+#pragma once
+#include "internal.h"
+
+namespace dg {
+
+constexpr int kRedBlocks = 304;   // 2 x 152 SMs; fixed so that reductions are reproducible
+constexpr int kRedThreads = 256;
+constexpr int kMaxCheb = 64;
+
+struct SmState {        // smoother scalars (device)
+    double rr, rr_new, pAp, a, beta, lam, a_prev, b_prev;
+    int stop, have_prev, skip, pad;
+    double ca[kMaxCheb], cb[kMaxCheb];
+};
+
+struct FcgState {       // flexible-CG scalars (device)
+    double dots[4];     // v.r, v.w, v.q, r.r
+    double rho, g, c;
+    int k, breakdown;
+};
+
+struct Red {            // reduction scratch: partials[kRedBlocks * 4] + results[4]
+    double* partials;
+    double* out;
+};
+
+// out[0..k) = dot products of (a_i, b_i) pairs, T in {float, double}, accumulated in double.
+template <typename T>
+cudaError_t dots(const T* const* a, const T* const* b, int k, long long n, Red red, cudaStream_t st);
+
+cudaError_t cast_d2f(const double* s, float* d, long long n, cudaStream_t st);
+cudaError_t cast_f2d(const float* s, double* d, long long n, cudaStream_t st);
+
+// r = b - y; p = r (if p); partial r.r into red (then finalize -> out[0])
+template <typename T>
+cudaError_t residual_init(const T* b, const T* y, T* r, T* p, long long n, Red red, cudaStream_t st);
+
+// CGEIGS pieces
+cudaError_t sm_init(SmState* s, const double* rr, cudaStream_t st);
+cudaError_t sm_alpha(SmState* s, const double* pAp, cudaStream_t st);
+template <typename T>
+cudaError_t cg_xr_update(const SmState* s, T* x, T* r, const T* p, const T* Ap, long long n, Red red, cudaStream_t st);
+cudaError_t sm_beta(SmState* s, const double* rr_new, cudaStream_t st);
+template <typename T>
+cudaError_t cg_p_update(const SmState* s, T* p, const T* r, long long n, cudaStream_t st);
+// Chebyshev
+cudaError_t sm_cheb_coeffs(SmState* s, int n_cheb, double Lambda, cudaStream_t st);
+template <typename T>
+cudaError_t cheb_step(const SmState* s, int k, const T* b, const T* Ax, T* p, T* x, long long n, cudaStream_t st);
+
+// FCG pieces (double vectors)
+cudaError_t fcg_scalars(FcgState* f, const double* dots3, int k, cudaStream_t st);
+cudaError_t fcg_dq(const FcgState* f, double* d, double* q, const double* v, const double* w, long long n,
+                   cudaStream_t st);
+cudaError_t fcg_update(const FcgState* f, double* u, double* r, const double* d, const double* q, long long n,
+                       Red red, cudaStream_t st);
+
+template <typename T>
+cudaError_t axpby(T a, const T* x, T b, T* y, long long n, cudaStream_t st);   // y = a x + b y
+template <typename T>
+cudaError_t sub3(const T* a, const T* b, T* c, long long n, cudaStream_t st);  // c = a - b
+
+// y = M x, M dense n x n (double, column-major), T vectors
+template <typename T>
+cudaError_t dense_matvec(const double* M, const T* x, T* y, int n, cudaStream_t st);
+
+}  // namespace dg

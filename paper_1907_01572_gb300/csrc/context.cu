@@ -1,0 +1,697 @@
+// C ABI entry points (include/dgell.h): context creation, operator apply,
+// smoother (Algs. 4-5), V-cycle (Alg. 3) and flexible CG (Alg. 2).
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "context.h"
+#include "geom.h"
+#include "source.h"
+
+using namespace dg;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t _e = (call);                                                         \
+        if (_e != cudaSuccess) return fail(DG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
+int resolve_level(dg_ctx* c, int level) {
+    if (level < 0) level = (int)c->lv.size() - 1;
+    return level;
+}
+
+template <typename T>
+LevelView<T> view(dg_ctx* c, int l);
+
+template <>
+LevelView<double> view<double>(dg_ctx* c, int l) {
+    LevelDev& L = c->lv[l];
+    LevelView<double> v{};
+    v.n_elems = L.h.n_elems();
+    v.p = L.p;
+    v.dof_off = L.dof_off;
+    v.vqp_off = L.vqp_off;
+    v.G = L.G64;
+    v.c0 = L.c0_64;
+    v.Ob = L.Ob64;
+    v.Ob_off = L.Ob_off;
+    v.slot_off = L.slot_off;
+    v.slot_mortar = L.slot_mortar;
+    v.slot_face = L.slot_face;
+    v.slot_side = L.slot_side;
+    v.mortars = L.mortars;
+    v.mg = L.mg64;
+    v.sigma = L.sigma64;
+    v.tab = c->tab64;
+    return v;
+}
+
+template <>
+LevelView<float> view<float>(dg_ctx* c, int l) {
+    LevelDev& L = c->lv[l];
+    LevelView<float> v{};
+    v.n_elems = L.h.n_elems();
+    v.p = L.p;
+    v.dof_off = L.dof_off;
+    v.vqp_off = L.vqp_off;
+    v.G = L.G32;
+    v.c0 = L.c0_32;
+    v.Ob = L.Ob32;
+    v.Ob_off = L.Ob_off;
+    v.slot_off = L.slot_off;
+    v.slot_mortar = L.slot_mortar;
+    v.slot_face = L.slot_face;
+    v.slot_side = L.slot_side;
+    v.mortars = L.mortars;
+    v.mg = L.mg32;
+    v.sigma = L.sigma32;
+    v.tab = c->tab32;
+    return v;
+}
+
+template <typename T>
+const T* tab_of(dg_ctx* c);
+template <>
+const double* tab_of<double>(dg_ctx* c) { return c->tab64; }
+template <>
+const float* tab_of<float>(dg_ctx* c) { return c->tab32; }
+
+template <typename T>
+Work<T>& work_of(LevelDev& L);
+template <>
+Work<double>& work_of<double>(LevelDev& L) { return L.w64; }
+template <>
+Work<float>& work_of<float>(LevelDev& L) { return L.w32; }
+
+template <typename T>
+int apply_t(dg_ctx* c, int l, const T* x, T* y) {
+    int launches = 0;
+    CK(launch_apply<T>(view<T>(c, l), c->lv[l].buckets, x, y, c->st, &launches));
+    c->launches += launches;
+    return DG_OK;
+}
+
+template <typename T>
+int ensure_work(dg_ctx* c, int l) {
+    Work<T>& W = work_of<T>(c->lv[l]);
+    if (W.ready) return DG_OK;
+    const size_t n = (size_t)c->lv[l].h.n_dofs();
+    W.f = c->arena.alloc<T>(n);
+    W.v = c->arena.alloc<T>(n);
+    W.r = c->arena.alloc<T>(n);
+    W.p = c->arena.alloc<T>(n);
+    W.Ap = c->arena.alloc<T>(n);
+    W.t = c->arena.alloc<T>(n);
+    W.sm = c->arena.alloc<SmState>(1);
+    if (c->arena.failed) return fail(DG_ERR_OOM, "device allocation failed (solver workspace)");
+    W.ready = true;
+    return DG_OK;
+}
+
+void cheb_defaults(const dg_cheb_opts* o, int& ne, int& nc, double& Lam) {
+    ne = (o && o->n_eigs > 0) ? o->n_eigs : 15;
+    nc = (o && o->n_cheb > 0) ? o->n_cheb : 15;
+    Lam = (o && o->Lambda > 0) ? o->Lambda : 20.0;
+    if (nc > kMaxCheb) nc = kMaxCheb;
+}
+
+// Alg. 4 with Alg. 5: smooths J x = b in place on level l.
+template <typename T>
+int smooth_t(dg_ctx* c, int l, const T* b, T* x, const dg_cheb_opts* o) {
+    int rc = ensure_work<T>(c, l);
+    if (rc) return rc;
+    int ne, nc;
+    double Lam;
+    cheb_defaults(o, ne, nc, Lam);
+    Work<T>& W = work_of<T>(c->lv[l]);
+    const long long n = c->lv[l].h.n_dofs();
+    cudaStream_t st = c->st;
+    if ((rc = apply_t<T>(c, l, x, W.Ap))) return rc;
+    CK(residual_init<T>(b, W.Ap, W.r, W.p, n, c->red, st));
+    CK(sm_init(W.sm, c->red.out, st));
+    c->launches += 3;
+    for (int k = 0; k < ne; ++k) {
+        if ((rc = apply_t<T>(c, l, W.p, W.Ap))) return rc;
+        const T* a[1] = {W.p};
+        const T* bb[1] = {W.Ap};
+        CK(dots<T>(a, bb, 1, n, c->red, st));
+        CK(sm_alpha(W.sm, c->red.out, st));
+        CK(cg_xr_update<T>(W.sm, x, W.r, W.p, W.Ap, n, c->red, st));
+        CK(sm_beta(W.sm, c->red.out, st));
+        CK(cg_p_update<T>(W.sm, W.p, W.r, n, st));
+        c->launches += 7;
+    }
+    CK(sm_cheb_coeffs(W.sm, nc, Lam, st));
+    CK(cudaMemsetAsync(W.p, 0, n * sizeof(T), st));
+    c->launches += 1;
+    for (int k = 0; k < nc; ++k) {
+        if ((rc = apply_t<T>(c, l, x, W.Ap))) return rc;
+        CK(cheb_step<T>(W.sm, k, b, W.Ap, W.p, x, n, st));
+        c->launches += 1;
+    }
+    return DG_OK;
+}
+
+template <typename T>
+TransferView<T> tview(dg_ctx* c, int lc) {
+    LevelDev& H = c->lv[lc];
+    LevelDev& h = c->lv[lc + 1];
+    TransferView<T> t{};
+    t.n_coarse = H.h.n_elems();
+    t.n_fine = h.h.n_elems();
+    t.pH = H.p;
+    t.ph = h.p;
+    t.dofH = H.dof_off;
+    t.dofh = h.dof_off;
+    t.child_off = H.child_off;
+    t.child_id = H.child_id;
+    t.child_bits = H.child_bits;
+    t.fine_parent = H.fine_parent;
+    t.fine_bits = H.fine_bits;
+    t.tab = tab_of<T>(c);
+    return t;
+}
+
+// coarse-grid solve support: dense inverse of the level-0 operator (FP64),
+// assembled column by column with the matrix-free apply.
+int ensure_coarse_inverse(dg_ctx* c) {
+    if (c->coarse_ready) return DG_OK;
+    const int n = (int)c->lv[0].h.n_dofs();
+    if (n > 4096) return fail(DG_ERR_UNSUPPORTED, "coarse Cholesky needs level 0 with at most 4096 dofs");
+    double* E = nullptr;
+    double* A = nullptr;
+    CK(cudaMalloc(&E, sizeof(double) * n * (size_t)n));
+    CK(cudaMalloc(&A, sizeof(double) * n * (size_t)n));
+    std::vector<double> h((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) h[(size_t)i * n + i] = 1.0;
+    CK(cudaMemcpyAsync(E, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, c->st));
+    for (int j = 0; j < n; ++j) {
+        int rc = apply_t<double>(c, 0, E + (size_t)j * n, A + (size_t)j * n);
+        if (rc) return rc;
+    }
+    CK(cudaMemcpyAsync(h.data(), A, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    cudaFree(E);
+    cudaFree(A);
+    // symmetric part, Cholesky L L^T, then the inverse column by column
+    std::vector<double> M((size_t)n * n);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) M[(size_t)i * n + j] = 0.5 * (h[(size_t)i * n + j] + h[(size_t)j * n + i]);
+    std::vector<double> Lc((size_t)n * n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        double s = M[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k) s -= Lc[(size_t)j * n + k] * Lc[(size_t)j * n + k];
+        if (!(s > 0.0)) return fail(DG_ERR_BREAKDOWN, "level-0 operator is not positive definite");
+        const double djj = std::sqrt(s);
+        Lc[(size_t)j * n + j] = djj;
+        for (int i = j + 1; i < n; ++i) {
+            double t = M[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k) t -= Lc[(size_t)i * n + k] * Lc[(size_t)j * n + k];
+            Lc[(size_t)i * n + j] = t / djj;
+        }
+    }
+    std::vector<double> inv((size_t)n * n, 0.0), z(n);
+    for (int col = 0; col < n; ++col) {
+        for (int i = 0; i < n; ++i) {
+            double t = (i == col) ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) t -= Lc[(size_t)i * n + k] * z[k];
+            z[i] = t / Lc[(size_t)i * n + i];
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            double t = z[i];
+            for (int k = i + 1; k < n; ++k) t -= Lc[(size_t)k * n + i] * inv[(size_t)col * n + k];
+            inv[(size_t)col * n + i] = t / Lc[(size_t)i * n + i];
+        }
+    }
+    c->coarse_inv = c->arena.alloc<double>((size_t)n * n);
+    if (!c->coarse_inv) return fail(DG_ERR_OOM, "device allocation failed (coarse inverse)");
+    CK(cudaMemcpyAsync(c->coarse_inv, inv.data(), sizeof(double) * inv.size(), cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    c->coarse_n = n;
+    c->coarse_ready = true;
+    return DG_OK;
+}
+
+// Alg. 3: v = VCYCLE(f) on the finest level.
+template <typename T>
+int vcycle_t(dg_ctx* c, const T* f, T* v, const dg_mg_opts* o) {
+    const int Lt = (int)c->lv.size() - 1;
+    cudaStream_t st = c->st;
+    int rc;
+    for (int l = 0; l <= Lt; ++l)
+        if ((rc = ensure_work<T>(c, l))) return rc;
+    if (o && o->coarse == 1 && (rc = ensure_coarse_inverse(c))) return rc;
+    const dg_cheb_opts* co = o ? &o->cheb : nullptr;
+    auto F = [&](int l) -> const T* { return l == Lt ? f : work_of<T>(c->lv[l]).f; };
+    auto V = [&](int l) -> T* { return l == Lt ? v : work_of<T>(c->lv[l]).v; };
+    for (int l = Lt; l >= 1; --l) {
+        const long long n = c->lv[l].h.n_dofs();
+        Work<T>& W = work_of<T>(c->lv[l]);
+        CK(cudaMemsetAsync(V(l), 0, n * sizeof(T), st));
+        if ((rc = smooth_t<T>(c, l, F(l), V(l), co))) return rc;
+        if ((rc = apply_t<T>(c, l, V(l), W.t))) return rc;
+        CK(sub3<T>(F(l), W.t, W.r, n, st));
+        CK(launch_restrict<T>(tview<T>(c, l - 1), W.r, work_of<T>(c->lv[l - 1]).f, st));
+        c->launches += 2;
+    }
+    {
+        const long long n0 = c->lv[0].h.n_dofs();
+        if (o && o->coarse == 1) {
+            CK(dense_matvec<T>(c->coarse_inv, F(0), V(0), (int)n0, st));
+            c->launches += 1;
+        } else {
+            CK(cudaMemsetAsync(V(0), 0, n0 * sizeof(T), st));
+            if ((rc = smooth_t<T>(c, 0, F(0), V(0), co))) return rc;
+        }
+    }
+    for (int l = 1; l <= Lt; ++l) {
+        CK(launch_prolong_add<T>(tview<T>(c, l - 1), V(l - 1), V(l), st));
+        c->launches += 1;
+        if ((rc = smooth_t<T>(c, l, F(l), V(l), co))) return rc;
+    }
+    return DG_OK;
+}
+
+int upload_level(dg_ctx* c, LevelDev& L, int li, std::string& err) {
+    Arena& A = c->arena;
+    cudaStream_t st = c->st;
+    LevelHost& h = L.h;
+    L.leaves = A.upload(h.leaves, st);
+    L.p = A.upload(h.p, st);
+    L.dof_off = A.upload(h.dof_off, st);
+    L.vqp_off = A.upload(h.vqp_off, st);
+    L.mortars = A.upload(h.mortars, st);
+    L.slot_off = A.upload(h.slot_off, st);
+    L.slot_mortar = A.upload(h.slot_mortar, st);
+    L.slot_face = A.upload(h.slot_face, st);
+    L.slot_side = A.upload(h.slot_side, st);
+    for (int n = kMinN; n <= kMaxN; ++n) {
+        BucketInfo& b = L.buckets[n];
+        b.count = (int)h.buckets[n].size();
+        b.elems = b.count ? A.upload(h.buckets[n], st) : nullptr;
+        b.max_q = 2;
+        b.max_nb = 2;
+        for (int e : h.buckets[n])
+            for (int s = h.slot_off[e]; s < h.slot_off[e + 1]; ++s) {
+                const Mortar& m = h.mortars[h.slot_mortar[s]];
+                b.max_q = std::max(b.max_q, (int)m.q);
+                const int o = h.slot_side[s] == 0 ? m.eB : m.eA;
+                if (o >= 0) b.max_nb = std::max(b.max_nb, h.p[o] + 1);
+            }
+    }
+    if (li + 1 < (int)c->lv.size()) {
+        L.child_off = A.upload(h.child_off, st);
+        L.child_id = A.upload(h.child_id, st);
+        L.child_bits = A.upload(h.child_bits, st);
+        L.fine_parent = A.upload(h.fine_parent, st);
+        L.fine_bits = A.upload(h.fine_bits, st);
+    }
+    const long long nv = h.vqp_off.back(), nd = h.n_dofs(), nm = h.n_mortar_pts, nb = h.n_bnd_pts;
+    const int nmort = (int)h.mortars.size();
+    L.G64 = A.alloc<double>(6 * nv);
+    L.wdetJ = A.alloc<double>(nv);
+    L.vxyz = A.alloc<double>(3 * nv);
+    L.mg64 = A.alloc<double>(7 * nm);
+    L.sigma64 = A.alloc<double>(nmort);
+    L.bxyz = A.alloc<double>(3 * nb);
+    L.G32 = A.alloc<float>(6 * nv);
+    L.mg32 = A.alloc<float>(7 * nm);
+    L.sigma32 = A.alloc<float>(nmort);
+    int* bad = A.alloc<int>(1);
+    double* X = nullptr;
+    if (A.failed || cudaMalloc(&X, sizeof(double) * 3 * nd) != cudaSuccess) {
+        err = "device allocation failed (geometry)";
+        return DG_ERR_OOM;
+    }
+    cudaMemsetAsync(bad, 0, sizeof(int), st);
+    GeomArgs g{};
+    g.n_elems = h.n_elems();
+    g.leaves = L.leaves;
+    g.p = L.p;
+    g.dof_off = L.dof_off;
+    g.vqp_off = L.vqp_off;
+    g.tab = c->tab64;
+    for (int d = 0; d < 3; ++d) {
+        g.lo[d] = c->desc.lo[d];
+        g.hi[d] = c->desc.hi[d];
+        g.warp_k[d] = c->desc.warp_k[d];
+    }
+    g.map_kind = c->desc.map_kind;
+    g.warp_amp = c->desc.warp_amp;
+    cudaError_t e1 = launch_node_coords(g, X, st);
+    cudaError_t e2 = launch_volume_geom(g, X, L.G64, L.wdetJ, L.vxyz, nv, bad, st);
+    cudaError_t e3 = launch_mortar_geom(g, X, L.mortars, nmort, c->C, L.mg64, L.sigma64, L.bxyz, nb, bad, st);
+    cudaError_t e4 = cast_d2f(L.G64, L.G32, 6 * nv, st);
+    cudaError_t e5 = cast_d2f(L.mg64, L.mg32, 7 * nm, st);
+    cudaError_t e6 = cast_d2f(L.sigma64, L.sigma32, nmort, st);
+    int hbad = 0;
+    cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaError_t e7 = cudaStreamSynchronize(st);
+    cudaFree(X);
+    c->launches += 6;
+    for (cudaError_t e : {e1, e2, e3, e4, e5, e6, e7})
+        if (e != cudaSuccess) {
+            err = std::string("geometry kernels: ") + cudaGetErrorString(e);
+            return DG_ERR_CUDA;
+        }
+    if (hbad) {
+        err = "non-positive Jacobian determinant at a GL point (block map folds an element)";
+        return DG_ERR_INVALID;
+    }
+    return DG_OK;
+}
+
+bool validate_desc(const dg_mesh_desc* d, std::string& err) {
+    if (!d || d->n_elems <= 0 || !d->leaves || !d->p) { err = "mesh description is empty"; return false; }
+    for (int k = 0; k < 3; ++k)
+        if (!(d->hi[k] > d->lo[k])) { err = "box must have hi > lo"; return false; }
+    if (d->map_kind != DG_MAP_AFFINE && d->map_kind != DG_MAP_SINE_WARP) { err = "unknown map kind"; return false; }
+    return true;
+}
+
+int build_hierarchy(const dg_mesh_desc* d, std::vector<LevelHost>& levels, std::string& err) {
+    LevelHost fine;
+    fine.leaves.assign(d->leaves, d->leaves + 4 * (size_t)d->n_elems);
+    fine.p.assign(d->p, d->p + d->n_elems);
+    if (!build_level_connectivity(fine, err)) return DG_ERR_INVALID;
+    std::vector<LevelHost> fine_first;
+    fine_first.push_back(std::move(fine));
+    while (true) {
+        LevelHost coarse;
+        std::string e2;
+        if (!coarsen_level(fine_first.back(), coarse, e2)) {
+            if (!e2.empty()) { err = e2; return DG_ERR_INVALID; }
+            break;
+        }
+        fine_first.push_back(std::move(coarse));
+    }
+    levels.assign(fine_first.rbegin(), fine_first.rend());
+    return DG_OK;
+}
+
+size_t level_bytes(const LevelHost& h) {
+    const size_t nv = h.vqp_off.back(), nd = h.n_dofs(), nm = h.n_mortar_pts;
+    size_t b = 0;
+    b += nv * (6 * 8 + 8 + 24 + 6 * 4);        // G64, wdetJ, vxyz, G32
+    b += nm * 7 * (8 + 4);                     // mortar geometry
+    b += h.mortars.size() * (sizeof(Mortar) + 12);
+    b += h.slot_mortar.size() * 6 + h.n_elems() * 40;
+    b += nd * 6 * (8 + 4);                     // solver work vectors, both precisions
+    return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dgi_set_error(int code, const char* msg) { return fail(code, msg ? msg : ""); }
+
+int dg_version(void) { return DGELL_VERSION; }
+const char* dg_last_error(void) { return g_err.c_str(); }
+
+int dg_ctx_footprint(const dg_mesh_desc* mesh, const dg_disc_opts* opts, size_t* bytes) {
+    (void)opts;
+    std::string err;
+    if (!validate_desc(mesh, err)) return fail(DG_ERR_INVALID, err);
+    std::vector<LevelHost> lv;
+    int rc = build_hierarchy(mesh, lv, err);
+    if (rc) return fail(rc, err);
+    size_t b = 2 * TabIndex::Count * kTabStride * 12;
+    for (auto& h : lv) b += level_bytes(h);
+    b += lv.back().n_dofs() * 8 * 6;            // FCG vectors
+    if (bytes) *bytes = b;
+    return DG_OK;
+}
+
+int dg_ctx_create(const dg_mesh_desc* mesh, const dg_disc_opts* opts, void* stream, dg_ctx** out) {
+    if (!out) return fail(DG_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    std::string err;
+    if (!validate_desc(mesh, err)) return fail(DG_ERR_INVALID, err);
+    std::vector<LevelHost> lvh;
+    int rc = build_hierarchy(mesh, lvh, err);
+    if (rc) return fail(rc, err);
+    auto c = std::make_unique<dg_ctx>();
+    c->st = (cudaStream_t)stream;
+    c->C = (opts && opts->penalty_c > 0) ? opts->penalty_c : 10.0;
+    c->desc = *mesh;
+    c->desc.leaves = nullptr;
+    c->desc.p = nullptr;
+    std::vector<double> tab;
+    build_tables(tab);
+    std::vector<float> tabf(tab.begin(), tab.end());
+    c->tab64 = c->arena.upload(tab, c->st);
+    c->tab32 = c->arena.upload(tabf, c->st);
+    c->red.partials = c->arena.alloc<double>(kRedBlocks * 4);
+    c->red.out = c->arena.alloc<double>(4);
+    c->fcg = c->arena.alloc<FcgState>(1);
+    if (c->arena.failed) {
+        c->arena.free_all();
+        return fail(DG_ERR_OOM, "device allocation failed");
+    }
+    if (cudaMallocHost(&c->red_host, 4 * sizeof(double)) != cudaSuccess) {
+        c->arena.free_all();
+        return fail(DG_ERR_CUDA, "pinned host allocation failed");
+    }
+    c->lv.resize(lvh.size());
+    for (size_t l = 0; l < lvh.size(); ++l) c->lv[l].h = std::move(lvh[l]);
+    for (size_t l = 0; l < c->lv.size(); ++l) {
+        rc = upload_level(c.get(), c->lv[l], (int)l, err);
+        if (rc) {
+            c->arena.free_all();
+            cudaFreeHost(c->red_host);
+            return fail(rc, err);
+        }
+    }
+    *out = c.release();
+    return DG_OK;
+}
+
+void dg_ctx_destroy(dg_ctx* c) {
+    if (!c) return;
+    if (c->st) cudaStreamSynchronize(c->st);
+    else cudaDeviceSynchronize();
+    c->arena.free_all();
+    if (c->red_host) cudaFreeHost(c->red_host);
+    delete c;
+}
+
+int dg_level_info_get(dg_ctx* c, int level, dg_level_info* info) {
+    if (!c || !info) return fail(DG_ERR_INVALID, "NULL argument");
+    level = resolve_level(c, level);
+    if (level < 0 || level >= (int)c->lv.size()) return fail(DG_ERR_INVALID, "level out of range");
+    const LevelHost& h = c->lv[level].h;
+    info->n_levels = (int)c->lv.size();
+    info->n_elems = h.n_elems();
+    info->n_dofs = h.n_dofs();
+    info->n_vol_qp = h.vqp_off.back();
+    info->n_bnd_qp = h.n_bnd_pts;
+    info->n_mortars = (int)h.mortars.size();
+    int mp = 0;
+    for (int v : h.p) mp = std::max(mp, v);
+    info->max_p = mp;
+    info->device_bytes = c->arena.bytes;
+    return DG_OK;
+}
+
+int dg_level_leaves(dg_ctx* c, int level, int* leaves, int* p, int64_t* dof_off) {
+    if (!c) return fail(DG_ERR_INVALID, "NULL context");
+    level = resolve_level(c, level);
+    if (level < 0 || level >= (int)c->lv.size()) return fail(DG_ERR_INVALID, "level out of range");
+    const LevelHost& h = c->lv[level].h;
+    if (leaves) std::memcpy(leaves, h.leaves.data(), h.leaves.size() * sizeof(int));
+    if (p) std::memcpy(p, h.p.data(), h.p.size() * sizeof(int));
+    if (dof_off)
+        for (size_t i = 0; i < h.dof_off.size(); ++i) dof_off[i] = h.dof_off[i];
+    return DG_OK;
+}
+
+int dg_quadrature_points(dg_ctx* c, int level, double* vol_xyz, double* bnd_xyz) {
+    if (!c) return fail(DG_ERR_INVALID, "NULL context");
+    level = resolve_level(c, level);
+    if (level < 0 || level >= (int)c->lv.size()) return fail(DG_ERR_INVALID, "level out of range");
+    LevelDev& L = c->lv[level];
+    if (vol_xyz) CK(cudaMemcpyAsync(vol_xyz, L.vxyz, sizeof(double) * 3 * L.h.vqp_off.back(), cudaMemcpyDeviceToDevice, c->st));
+    if (bnd_xyz && L.h.n_bnd_pts)
+        CK(cudaMemcpyAsync(bnd_xyz, L.bxyz, sizeof(double) * 3 * L.h.n_bnd_pts, cudaMemcpyDeviceToDevice, c->st));
+    return DG_OK;
+}
+
+int dg_apply(dg_ctx* c, int level, int prec, const void* x, void* y) {
+    if (!c || !x || !y) return fail(DG_ERR_INVALID, "NULL argument");
+    level = resolve_level(c, level);
+    if (level < 0 || level >= (int)c->lv.size()) return fail(DG_ERR_INVALID, "level out of range");
+    if (x == y) return fail(DG_ERR_INVALID, "x and y must not alias");
+    if (prec == DG_FP64) return apply_t<double>(c, level, (const double*)x, (double*)y);
+    if (prec == DG_FP32) return apply_t<float>(c, level, (const float*)x, (float*)y);
+    return fail(DG_ERR_UNSUPPORTED, "precision not implemented");
+}
+
+int dg_convert(dg_ctx* c, int64_t n, int sp, const void* s, int dp, void* d) {
+    if (!c || !s || !d || n < 0) return fail(DG_ERR_INVALID, "bad argument");
+    if (sp == DG_FP64 && dp == DG_FP32) CK(cast_d2f((const double*)s, (float*)d, n, c->st));
+    else if (sp == DG_FP32 && dp == DG_FP64) CK(cast_f2d((const float*)s, (double*)d, n, c->st));
+    else if (sp == dp) CK(cudaMemcpyAsync(d, s, n * (sp == DG_FP64 ? 8 : 4), cudaMemcpyDeviceToDevice, c->st));
+    else return fail(DG_ERR_UNSUPPORTED, "conversion not implemented");
+    c->launches += 1;
+    return DG_OK;
+}
+
+int64_t dg_launch_count(dg_ctx* c) { return c ? c->launches : -1; }
+
+int dg_transfer(dg_ctx* c, int lc, int prec, int dir, const void* in, void* out) {
+    if (!c || !in || !out) return fail(DG_ERR_INVALID, "NULL argument");
+    if (lc < 0 || lc + 1 >= (int)c->lv.size()) return fail(DG_ERR_INVALID, "coarse level out of range");
+    if (dir != 0 && dir != 1) return fail(DG_ERR_INVALID, "direction must be 0 or 1");
+    if (prec == DG_FP64) {
+        if (dir == 0) CK(launch_prolong_add<double>(tview<double>(c, lc), (const double*)in, (double*)out, c->st));
+        else CK(launch_restrict<double>(tview<double>(c, lc), (const double*)in, (double*)out, c->st));
+    } else if (prec == DG_FP32) {
+        if (dir == 0) CK(launch_prolong_add<float>(tview<float>(c, lc), (const float*)in, (float*)out, c->st));
+        else CK(launch_restrict<float>(tview<float>(c, lc), (const float*)in, (float*)out, c->st));
+    } else {
+        return fail(DG_ERR_UNSUPPORTED, "precision not implemented");
+    }
+    c->launches += 1;
+    return DG_OK;
+}
+
+int dg_smooth(dg_ctx* c, int level, int prec, const void* b, void* x, const dg_cheb_opts* opts, double* lam_out) {
+    if (!c || !b || !x) return fail(DG_ERR_INVALID, "NULL argument");
+    level = resolve_level(c, level);
+    if (level < 0 || level >= (int)c->lv.size()) return fail(DG_ERR_INVALID, "level out of range");
+    int rc;
+    if (prec == DG_FP64) rc = smooth_t<double>(c, level, (const double*)b, (double*)x, opts);
+    else if (prec == DG_FP32) rc = smooth_t<float>(c, level, (const float*)b, (float*)x, opts);
+    else return fail(DG_ERR_UNSUPPORTED, "precision not implemented");
+    if (rc) return rc;
+    if (lam_out) {
+        SmState* sm = prec == DG_FP64 ? c->lv[level].w64.sm : c->lv[level].w32.sm;
+        CK(cudaMemcpyAsync(c->red_host, &sm->lam, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        *lam_out = c->red_host[0];
+    }
+    return DG_OK;
+}
+
+int dg_vcycle(dg_ctx* c, int prec, const void* f, void* v, const dg_mg_opts* opts) {
+    if (!c || !f || !v) return fail(DG_ERR_INVALID, "NULL argument");
+    if (prec == DG_FP64) return vcycle_t<double>(c, (const double*)f, (double*)v, opts);
+    if (prec == DG_FP32) return vcycle_t<float>(c, (const float*)f, (float*)v, opts);
+    return fail(DG_ERR_UNSUPPORTED, "precision not implemented");
+}
+
+int dg_solve(dg_ctx* c, const double* b, double* x, const dg_solver_opts* o, dg_solve_stats* stats) {
+    if (!c || !b || !x) return fail(DG_ERR_INVALID, "NULL argument");
+    auto t0 = std::chrono::steady_clock::now();
+    const int Lt = (int)c->lv.size() - 1;
+    const long long n = c->lv[Lt].h.n_dofs();
+    const double tol = (o && o->tol > 0) ? o->tol : 1e-10;
+    const int maxit = (o && o->max_iter > 0) ? o->max_iter : 100;
+    const int mgp = o ? o->mg_prec : DG_FP64;
+    const bool use_mg = o ? o->use_mg != 0 : true;
+    const dg_mg_opts* mo = o ? &o->mg : nullptr;
+    cudaStream_t st = c->st;
+    if (!c->fcg_vec[0]) {
+        for (int i = 0; i < 6; ++i) c->fcg_vec[i] = c->arena.alloc<double>(n);
+        for (int i = 0; i < 2; ++i) c->fcg32[i] = c->arena.alloc<float>(n);
+        if (c->arena.failed) return fail(DG_ERR_OOM, "device allocation failed (FCG vectors)");
+    }
+    double *r = c->fcg_vec[0], *v = c->fcg_vec[1], *w = c->fcg_vec[2], *d = c->fcg_vec[3], *q = c->fcg_vec[4],
+           *t = c->fcg_vec[5];
+    int rc;
+    auto read_out = [&](int k, double* dst) -> int {
+        CK(cudaMemcpyAsync(c->red_host, c->red.out, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int i = 0; i < k; ++i) dst[i] = c->red_host[i];
+        return DG_OK;
+    };
+    // ||b||
+    {
+        const double* a[1] = {b};
+        CK(dots<double>(a, a, 1, n, c->red, st));
+    }
+    double nb2;
+    if ((rc = read_out(1, &nb2))) return rc;
+    const double nb = std::sqrt(nb2);
+    if ((rc = apply_t<double>(c, Lt, x, t))) return rc;
+    CK(residual_init<double>(b, t, r, nullptr, n, c->red, st));
+    double rr;
+    if ((rc = read_out(1, &rr))) return rc;
+    CK(cudaMemsetAsync(c->fcg, 0, sizeof(FcgState), st));
+    int k = 0;
+    double rel = nb > 0 ? std::sqrt(rr) / nb : 0.0;
+    int status = DG_OK;
+    while (k < maxit && rel >= tol && nb > 0) {
+        // v = VCYCLE(r)
+        if (!use_mg) {
+            CK(cudaMemcpyAsync(v, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        } else if (mgp == DG_FP32) {
+            CK(cast_d2f(r, c->fcg32[0], n, st));
+            if ((rc = vcycle_t<float>(c, c->fcg32[0], c->fcg32[1], mo))) return rc;
+            CK(cast_f2d(c->fcg32[1], v, n, st));
+            c->launches += 2;
+        } else {
+            if ((rc = vcycle_t<double>(c, r, v, mo))) return rc;
+        }
+        if ((rc = apply_t<double>(c, Lt, v, w))) return rc;
+        {
+            const double* a[3] = {v, v, v};
+            const double* bb[3] = {r, w, q};
+            CK(dots<double>(a, bb, k == 0 ? 2 : 3, n, c->red, st));
+        }
+        CK(fcg_scalars(c->fcg, c->red.out, k, st));
+        if (k == 0) {
+            CK(cudaMemcpyAsync(d, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(q, w, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        } else {
+            CK(fcg_dq(c->fcg, d, q, v, w, n, st));
+        }
+        CK(fcg_update(c->fcg, x, r, d, q, n, c->red, st));
+        c->launches += 6;
+        if ((rc = read_out(1, &rr))) return rc;
+        FcgState fs;
+        CK(cudaMemcpyAsync(&fs, c->fcg, sizeof(FcgState), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        ++k;
+        if (fs.breakdown || !std::isfinite(rr)) {
+            status = DG_ERR_BREAKDOWN;
+            break;
+        }
+        rel = std::sqrt(rr) / nb;
+    }
+    // true residual
+    if ((rc = apply_t<double>(c, Lt, x, t))) return rc;
+    CK(sub3<double>(b, t, w, n, st));
+    {
+        const double* a[1] = {w};
+        CK(dots<double>(a, a, 1, n, c->red, st));
+    }
+    double tr2;
+    if ((rc = read_out(1, &tr2))) return rc;
+    const double true_rel = nb > 0 ? std::sqrt(tr2) / nb : 0.0;
+    if (status == DG_OK && rel >= tol && nb > 0) status = DG_ERR_NOT_CONVERGED;
+    if (stats) {
+        stats->iterations = k;
+        stats->rel_residual = true_rel;
+        stats->rel_residual_rec = rel;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        stats->status = status;
+    }
+    if (status == DG_ERR_BREAKDOWN) return fail(status, "flexible CG breakdown (non-positive rho)");
+    if (status == DG_ERR_NOT_CONVERGED) return fail(status, "flexible CG reached max_iter");
+    return DG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,93 @@
+// Context: device-resident hierarchy, geometry, tables and solver workspaces.
+#pragma once
+#include <memory>
+
+#include "apply.h"
+#include "blas.h"
+#include "internal.h"
+#include "transfer.h"
+
+namespace dg {
+
+struct Arena {
+    std::vector<void*> ptrs;
+    size_t bytes = 0;
+    bool failed = false;
+    template <typename T>
+    T* alloc(size_t n) {
+        if (n == 0) n = 1;
+        void* p = nullptr;
+        if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) {
+            cudaGetLastError();
+            failed = true;
+            return nullptr;
+        }
+        ptrs.push_back(p);
+        bytes += n * sizeof(T);
+        return static_cast<T*>(p);
+    }
+    template <typename T>
+    T* upload(const std::vector<T>& v, cudaStream_t st) {
+        T* d = alloc<T>(v.size());
+        if (d && !v.empty()) cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+        return d;
+    }
+    void free_all() {
+        for (void* p : ptrs) cudaFree(p);
+        ptrs.clear();
+    }
+};
+
+template <typename T>
+struct Work {
+    T *f = nullptr, *v = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr, *t = nullptr;
+    SmState* sm = nullptr;
+    bool ready = false;
+};
+
+struct LevelDev {
+    LevelHost h;
+    int *leaves = nullptr, *p = nullptr;
+    long long *dof_off = nullptr, *vqp_off = nullptr;
+    Mortar* mortars = nullptr;
+    int *slot_off = nullptr, *slot_mortar = nullptr;
+    unsigned char *slot_face = nullptr, *slot_side = nullptr;
+    BucketInfo buckets[kMaxN + 1] = {};
+    double *G64 = nullptr, *wdetJ = nullptr, *vxyz = nullptr, *mg64 = nullptr, *sigma64 = nullptr, *bxyz = nullptr;
+    float *G32 = nullptr, *mg32 = nullptr, *sigma32 = nullptr;
+    double* c0_64 = nullptr;
+    float* c0_32 = nullptr;
+    double* Ob64 = nullptr;
+    float* Ob32 = nullptr;
+    long long* Ob_off = nullptr;
+    // transfer to the next finer level (this level is the coarse side)
+    int *child_off = nullptr, *child_id = nullptr, *fine_parent = nullptr;
+    unsigned char *child_bits = nullptr, *fine_bits = nullptr;
+    Work<double> w64;
+    Work<float> w32;
+};
+
+}  // namespace dg
+
+struct dg_ctx {
+    cudaStream_t st = nullptr;
+    double C = 10.0;
+    dg_mesh_desc desc{};
+    std::vector<dg::LevelDev> lv;   // 0 = coarsest
+    dg::Arena arena;
+    double* tab64 = nullptr;
+    float* tab32 = nullptr;
+    dg::Red red{};
+    double* red_host = nullptr;     // pinned, 4 doubles
+    dg::FcgState* fcg = nullptr;
+    double* fcg_vec[6] = {};        // r, v, w, d, q, t (double, finest)
+    float* fcg32[2] = {};           // f32 copies of r and v for the mixed-precision V-cycle
+    double* coarse_inv = nullptr;   // dense inverse of the level-0 operator
+    int coarse_n = 0;
+    bool coarse_ready = false;
+    bool has_zeroth = false;
+    // puncture data on the finest level volume points
+    double* p_alpha = nullptr;
+    double* p_beta = nullptr;
+    long long launches = 0;
+};

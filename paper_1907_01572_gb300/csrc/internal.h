@@ -1,0 +1,120 @@
+// Internal data model of libdgell (host + device).  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dgell.h"
+
+namespace dg {
+
+constexpr int kMaxN = 9;          // n = p + 1 <= 9 (p <= 8)
+constexpr int kMinN = 2;
+constexpr int kNumN = kMaxN - kMinN + 1;
+constexpr int kTabStride = 81;    // every 1-D table is stored padded to 9 x 9
+
+// ---- 1-D operator tables (Sec. II.F.4: interpolation / derivative operators
+// of size (p'+1) x (p+1), kept for every degree pair) -------------------------
+// Layout (values of type T, each matrix row-major, padded to 9x9):
+//   I  [n]          : I[i][a]  = l_a(x^GL_i)               (LGL -> GL, n x n)
+//   Dg [n]          : Dg[i][j] = l^GL_j'(x^GL_i)           (GL collocation derivative)
+//   DL [n]          : DL[i][a] = l_a'(x^LGL_i)             (LGL collocation derivative)
+//   IDg[n]          : IDg[i][a]= l_a'(x^GL_i)              (derivative at GL points)
+//   Im [n][q][pos]  : Im[i][a] = l_a(m_pos(s_i))           (face LGL -> mortar GL, q x n)
+//   Dm [n][q][pos]  : Dm[i][a] = l_a'(m_pos(s_i))
+//   CI [nH][nh][b]  : CI[i][a] = l^H_a((x^h_i + 2b - 1)/2) (parent -> child half b, nh x nH)
+// m_pos: 0 -> s, 1 -> (s - 1)/2, 2 -> (s + 1)/2.
+struct TabIndex {
+    static constexpr int I = 0;
+    static constexpr int Dg = I + kNumN;
+    static constexpr int DL = Dg + kNumN;
+    static constexpr int IDg = DL + kNumN;
+    static constexpr int Im = IDg + kNumN;
+    static constexpr int Dm = Im + kNumN * kNumN * 3;
+    static constexpr int CI = Dm + kNumN * kNumN * 3;
+    static constexpr int LGLx = CI + kNumN * kNumN * 2;   // 1 row: LGL nodes of n
+    static constexpr int GLx = LGLx + kNumN;              // GL nodes of q
+    static constexpr int GLw = GLx + kNumN;               // GL weights of q
+    static constexpr int Count = GLw + kNumN;
+};
+
+__host__ __device__ inline int tab_n(int base, int n) { return (base + (n - kMinN)) * kTabStride; }
+__host__ __device__ inline int tab_m(int base, int n, int q, int pos) {
+    return (base + ((n - kMinN) * kNumN + (q - kMinN)) * 3 + pos) * kTabStride;
+}
+__host__ __device__ inline int tab_ci(int nH, int nh, int b) {
+    return (TabIndex::CI + ((nH - kMinN) * kNumN + (nh - kMinN)) * 2 + b) * kTabStride;
+}
+
+void build_tables(std::vector<double>& tab);   // size TabIndex::Count * kTabStride
+
+// ---- mesh ----------------------------------------------------------------------
+struct Mortar {            // device record (32 bytes)
+    int eA, eB;            // eA: geometry ('-') side = finer / lower index; eB = -1 on the boundary
+    unsigned char fA, fB;  // faces (2*dim + side)
+    unsigned char posA0, posA1, posB0, posB1;  // sub-face codes along the two tangential axes
+    unsigned char q;       // GL points per direction = p_m + 1
+    unsigned char pad;
+    long long goff;        // offset (in points) into the mortar geometry arrays
+    long long bnd_off;     // offset into boundary point arrays (-1 if interior)
+};
+
+struct LevelHost {
+    std::vector<int> leaves;         // 4 per element
+    std::vector<int> p;
+    std::vector<long long> dof_off;  // n_elems + 1
+    std::vector<long long> vqp_off;  // volume GL point offsets, n_elems + 1
+    std::vector<Mortar> mortars;
+    std::vector<int> slot_off;       // n_elems + 1
+    std::vector<int> slot_mortar;
+    std::vector<unsigned char> slot_face, slot_side;
+    long long n_mortar_pts = 0;
+    long long n_bnd_pts = 0;
+    // transfer to the next finer level (filled on levels < L):
+    //   per coarse element: child count (1 or 8) and children (fine ids) + bits
+    std::vector<int> child_off;      // n_elems + 1
+    std::vector<int> child_id;
+    std::vector<unsigned char> child_bits;   // bit0: x half, bit1: y, bit2: z; 0xFF: carried over
+    // per fine element of the next finer level: parent id and bits
+    std::vector<int> fine_parent;
+    std::vector<unsigned char> fine_bits;
+    int n_elems() const { return (int)p.size(); }
+    long long n_dofs() const { return dof_off.back(); }
+    std::vector<int> buckets[kMaxN + 1];  // element ids by n
+};
+
+// Builds the finest level's connectivity; returns false with a message on a malformed mesh.
+bool build_level_connectivity(LevelHost& L, std::string& err);
+// Coarsens `fine` into `coarse` (Sec. II.E.3); returns false when no family merges.
+bool coarsen_level(const LevelHost& fine, LevelHost& coarse, std::string& err);
+
+// ---- device level ------------------------------------------------------------------
+template <typename T>
+struct LevelView {         // passed by value to kernels
+    int n_elems;
+    const int* p;
+    const long long* dof_off;
+    const long long* vqp_off;
+    const T* G;            // 6 * n_vqp: G[6*vqp_off[e] + c*q^3 + pt]
+    const T* c0;           // zeroth-order coefficient (w det J f) per volume point or nullptr
+    const T* Ob;           // dense Galerkin blocks (coarse levels) or nullptr
+    const long long* Ob_off;
+    const int* slot_off;
+    const int* slot_mortar;
+    const unsigned char* slot_face;
+    const unsigned char* slot_side;
+    const Mortar* mortars;
+    const T* mg;           // 7 * n_mortar_pts: [wS, cA0, cA1, cA2, cB0, cB1, cB2] blocks per mortar
+    const T* sigma;        // per mortar
+    const T* tab;
+};
+
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace dg

@@ -1,0 +1,296 @@
+"""Thin ctypes binding of the C ABI in include/dgell.h.
+
+Argument marshalling only: every computation runs in libdgell.so's CUDA
+kernels.  Device vectors are torch CUDA tensors (their data_ptr() is passed);
+the context's stream is torch's current stream at creation unless one is
+given.  Loading fails loudly when the library has not been built.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdgell.so")
+
+DG_OK, DG_ERR_INVALID, DG_ERR_OOM, DG_ERR_CUDA, DG_ERR_NOT_CONVERGED, DG_ERR_BREAKDOWN, DG_ERR_UNSUPPORTED = range(7)
+DG_FP64, DG_FP32, DG_BF16 = 0, 1, 2
+DG_MAP_AFFINE, DG_MAP_SINE_WARP = 0, 1
+
+
+class DgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("dgell error %d: %s" % (code, msg))
+        self.code = code
+
+
+class dg_mesh_desc(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3), ("map_kind", ctypes.c_int),
+                ("warp_amp", ctypes.c_double), ("warp_k", ctypes.c_int * 3), ("n_elems", ctypes.c_int),
+                ("leaves", ctypes.POINTER(ctypes.c_int)), ("p", ctypes.POINTER(ctypes.c_int))]
+
+
+class dg_disc_opts(ctypes.Structure):
+    _fields_ = [("penalty_c", ctypes.c_double), ("reserved", ctypes.c_int * 4)]
+
+
+class dg_level_info(ctypes.Structure):
+    _fields_ = [("n_levels", ctypes.c_int), ("n_elems", ctypes.c_int), ("n_dofs", ctypes.c_int64),
+                ("n_vol_qp", ctypes.c_int64), ("n_bnd_qp", ctypes.c_int64), ("n_mortars", ctypes.c_int),
+                ("max_p", ctypes.c_int), ("device_bytes", ctypes.c_size_t)]
+
+
+class dg_cheb_opts(ctypes.Structure):
+    _fields_ = [("n_eigs", ctypes.c_int), ("n_cheb", ctypes.c_int), ("Lambda", ctypes.c_double)]
+
+
+class dg_mg_opts(ctypes.Structure):
+    _fields_ = [("cheb", dg_cheb_opts), ("coarse", ctypes.c_int)]
+
+
+class dg_solver_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mg_prec", ctypes.c_int),
+                ("use_mg", ctypes.c_int), ("mg", dg_mg_opts)]
+
+
+class dg_solve_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("rel_residual_rec", ctypes.c_double), ("seconds", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+class dg_puncture_params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("m", ctypes.c_double * 16), ("c", (ctypes.c_double * 3) * 16),
+                ("P", (ctypes.c_double * 3) * 16)]
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "dg_version": ([], ctypes.c_int),
+    "dg_last_error": ([], ctypes.c_char_p),
+    "dg_ctx_create": ([ctypes.POINTER(dg_mesh_desc), ctypes.POINTER(dg_disc_opts), _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "dg_ctx_destroy": ([_P], None),
+    "dg_ctx_footprint": ([ctypes.POINTER(dg_mesh_desc), ctypes.POINTER(dg_disc_opts), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "dg_level_info_get": ([_P, ctypes.c_int, ctypes.POINTER(dg_level_info)], ctypes.c_int),
+    "dg_level_leaves": ([_P, ctypes.c_int, _P, _P, _P], ctypes.c_int),
+    "dg_quadrature_points": ([_P, ctypes.c_int, _P, _P], ctypes.c_int),
+    "dg_apply": ([_P, ctypes.c_int, ctypes.c_int, _P, _P], ctypes.c_int),
+    "dg_rhs": ([_P, _P, _P, _P], ctypes.c_int),
+    "dg_smooth": ([_P, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.POINTER(dg_cheb_opts), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "dg_vcycle": ([_P, ctypes.c_int, _P, _P, ctypes.POINTER(dg_mg_opts)], ctypes.c_int),
+    "dg_solve": ([_P, _P, _P, ctypes.POINTER(dg_solver_opts), ctypes.POINTER(dg_solve_stats)], ctypes.c_int),
+    "dg_set_zeroth_order": ([_P, _P], ctypes.c_int),
+    "dg_puncture_setup": ([_P, ctypes.POINTER(dg_puncture_params)], ctypes.c_int),
+    "dg_puncture_residual": ([_P, _P, _P], ctypes.c_int),
+    "dg_newton_step": ([_P, _P, ctypes.POINTER(dg_solver_opts), ctypes.POINTER(dg_solve_stats), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "dg_newton_solve": ([_P, _P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(dg_solver_opts), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "dg_convert": ([_P, ctypes.c_int64, ctypes.c_int, _P, ctypes.c_int, _P], ctypes.c_int),
+    "dg_launch_count": ([_P], ctypes.c_int64),
+    "dg_transfer": ([_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P], ctypes.c_int),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded libdgell.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libdgell.so not built: run __graft_entry__.build() (nvcc, sm_103a)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != DG_OK:
+        raise DgError(rc, lib().dg_last_error().decode())
+    return rc
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _prec(t):
+    import torch
+    if t.dtype == torch.float64:
+        return DG_FP64
+    if t.dtype == torch.float32:
+        return DG_FP32
+    raise ValueError("vectors must be float64 or float32")
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def make_mesh_desc(desc):
+    """dg_mesh_desc from an inputs-style dict (keeps the arrays alive on the struct)."""
+    leaves = np.ascontiguousarray(np.asarray(desc["leaves"], dtype=np.int32).reshape(-1, 4))
+    p = np.ascontiguousarray(np.asarray(desc["p"], dtype=np.int32).ravel())
+    d = dg_mesh_desc()
+    for k in range(3):
+        d.lo[k] = float(desc["lo"][k])
+        d.hi[k] = float(desc["hi"][k])
+    if desc.get("warp") is None:
+        d.map_kind = DG_MAP_AFFINE
+    else:
+        d.map_kind = DG_MAP_SINE_WARP
+        d.warp_amp = float(desc["warp"][0])
+        for k in range(3):
+            d.warp_k[k] = int(desc["warp"][1][k])
+    d.n_elems = len(p)
+    d.leaves = leaves.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    d.p = p.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    d._keep = (leaves, p)
+    return d
+
+
+def dg_version():
+    return lib().dg_version()
+
+
+def dg_ctx_footprint(desc, penalty_c=10.0):
+    d = make_mesh_desc(desc)
+    o = dg_disc_opts(penalty_c)
+    b = ctypes.c_size_t(0)
+    _check(lib().dg_ctx_footprint(ctypes.byref(d), ctypes.byref(o), ctypes.byref(b)))
+    return b.value
+
+
+def cheb_opts(n_eigs=15, n_cheb=15, Lambda=20.0):
+    return dg_cheb_opts(n_eigs, n_cheb, Lambda)
+
+
+def mg_opts(n_eigs=15, n_cheb=15, Lambda=20.0, coarse=0):
+    return dg_mg_opts(cheb_opts(n_eigs, n_cheb, Lambda), coarse)
+
+
+def solver_opts(tol=1e-10, max_iter=100, mg_prec=DG_FP64, use_mg=1, **mg):
+    return dg_solver_opts(tol, max_iter, mg_prec, use_mg, mg_opts(**mg))
+
+
+class Context:
+    """Owns a dg_ctx; methods are the C calls of the same name without 'dg_'."""
+
+    def __init__(self, desc, penalty_c=10.0, stream=None):
+        d = make_mesh_desc(desc)
+        o = dg_disc_opts(penalty_c)
+        h = ctypes.c_void_p()
+        st = _stream() if stream is None else ctypes.c_void_p(stream)
+        _check(lib().dg_ctx_create(ctypes.byref(d), ctypes.byref(o), st, ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib().dg_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def level_info(self, level=-1):
+        i = dg_level_info()
+        _check(lib().dg_level_info_get(self.h, level, ctypes.byref(i)))
+        return {k: getattr(i, k) for k, _ in dg_level_info._fields_}
+
+    @property
+    def n_levels(self):
+        return self.level_info()["n_levels"]
+
+    def level_leaves(self, level=-1):
+        info = self.level_info(level)
+        ne = info["n_elems"]
+        leaves = np.zeros((ne, 4), dtype=np.int32)
+        p = np.zeros(ne, dtype=np.int32)
+        off = np.zeros(ne + 1, dtype=np.int64)
+        _check(lib().dg_level_leaves(self.h, level, leaves.ctypes.data, p.ctypes.data, off.ctypes.data))
+        return leaves, p, off
+
+    def quadrature_points(self, level=-1):
+        import torch
+        info = self.level_info(level)
+        v = torch.empty(3 * info["n_vol_qp"], dtype=torch.float64, device="cuda")
+        b = torch.empty(max(1, 3 * info["n_bnd_qp"]), dtype=torch.float64, device="cuda")
+        _check(lib().dg_quadrature_points(self.h, level, _ptr(v), _ptr(b)))
+        return v.view(3, -1), b[:3 * info["n_bnd_qp"]].view(3, -1)
+
+    def apply(self, x, y, level=-1):
+        _check(lib().dg_apply(self.h, level, _prec(x), _ptr(x), _ptr(y)))
+        return y
+
+    def rhs(self, g_qp, gD_qp, F):
+        _check(lib().dg_rhs(self.h, _ptr(g_qp), _ptr(gD_qp), _ptr(F)))
+        return F
+
+    def smooth(self, b, x, level=-1, n_eigs=15, n_cheb=15, Lambda=20.0, want_lambda=True):
+        o = cheb_opts(n_eigs, n_cheb, Lambda)
+        lam = ctypes.c_double(0.0)
+        _check(lib().dg_smooth(self.h, level, _prec(b), _ptr(b), _ptr(x), ctypes.byref(o),
+                               ctypes.byref(lam) if want_lambda else None))
+        return lam.value
+
+    def vcycle(self, f, v, **mg):
+        o = mg_opts(**mg)
+        _check(lib().dg_vcycle(self.h, _prec(f), _ptr(f), _ptr(v), ctypes.byref(o)))
+        return v
+
+    def solve(self, b, x, check=True, **kw):
+        o = solver_opts(**kw)
+        s = dg_solve_stats()
+        rc = lib().dg_solve(self.h, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(s))
+        if check:
+            _check(rc)
+        return {k: getattr(s, k) for k, _ in dg_solve_stats._fields_}
+
+    def set_zeroth_order(self, coef_qp):
+        _check(lib().dg_set_zeroth_order(self.h, _ptr(coef_qp)))
+
+    def puncture_setup(self, punctures):
+        prm = dg_puncture_params()
+        prm.n = len(punctures)
+        for i, (m, c, P) in enumerate(punctures):
+            prm.m[i] = m
+            for k in range(3):
+                prm.c[i][k] = c[k]
+                prm.P[i][k] = P[k]
+        _check(lib().dg_puncture_setup(self.h, ctypes.byref(prm)))
+
+    def puncture_residual(self, u, R):
+        _check(lib().dg_puncture_residual(self.h, _ptr(u), _ptr(R)))
+        return R
+
+    def newton_step(self, u, **kw):
+        o = solver_opts(**kw)
+        s = dg_solve_stats()
+        rn = ctypes.c_double(0.0)
+        _check(lib().dg_newton_step(self.h, _ptr(u), ctypes.byref(o), ctypes.byref(s), ctypes.byref(rn)))
+        return rn.value, {k: getattr(s, k) for k, _ in dg_solve_stats._fields_}
+
+    def newton_solve(self, u, tol=1e-10, max_newton=20, **kw):
+        o = solver_opts(**kw)
+        steps = ctypes.c_int(0)
+        rn = ctypes.c_double(0.0)
+        _check(lib().dg_newton_solve(self.h, _ptr(u), tol, max_newton, ctypes.byref(o), ctypes.byref(steps),
+                                     ctypes.byref(rn)))
+        return steps.value, rn.value
+
+    def convert(self, src, dst):
+        _check(lib().dg_convert(self.h, src.numel(), _prec(src), _ptr(src), _prec(dst), _ptr(dst)))
+        return dst
+
+    def transfer(self, coarse_level, direction, x, out):
+        _check(lib().dg_transfer(self.h, coarse_level, _prec(x), direction, _ptr(x), _ptr(out)))
+        return out
+
+    def launch_count(self):
+        return lib().dg_launch_count(self.h)

@@ -1,0 +1,136 @@
+"""GPU parity of the right-hand side (eq. equationFh2), the Chebyshev/CGEIGS
+smoother (Algs. 4-5), the V-cycle (Alg. 3) and the flexible-CG solve (Alg. 2)
+against the oracle, on the same seeded inputs."""
+import numpy as np
+import pytest
+
+from gpu_util import CASES, oracle_mesh, rel_l2
+from oracle import krylov, multigrid, sipg
+from paper_1907_01572_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    assert torch.cuda.is_available()
+    return torch
+
+
+_H = {}
+
+
+def hierarchy(name):
+    if name not in _H:
+        desc = CASES[name]()
+        m = oracle_mesh(desc)
+        _H[name] = (desc, m, multigrid.Hierarchy(m))
+    return _H[name]
+
+
+def u_exact(x):
+    return np.sin(np.pi * x[:, 0]) * np.sin(np.pi * x[:, 1]) * np.sin(np.pi * x[:, 2])
+
+
+def gD_fun(x):
+    return np.exp(0.3 * x[:, 0]) * np.cos(0.7 * x[:, 1]) + x[:, 2] ** 2
+
+
+@pytest.mark.parametrize("name", ["config1_affine_p3", "mixed_curved_2to1_l1"])
+def test_rhs_matches_oracle(name, torch):
+    from paper_1907_01572_gb300 import dgell
+    desc = CASES[name]()
+    m = oracle_mesh(desc)
+    ctx = dgell.Context(desc)
+    vxyz, bxyz = ctx.quadrature_points()
+    g = 3 * np.pi ** 2 * u_exact(vxyz.T.cpu().numpy())
+    gd = gD_fun(bxyz.T.cpu().numpy())
+    F = torch.empty(m.n_dofs, dtype=torch.float64, device="cuda")
+    ctx.rhs(torch.tensor(g, device="cuda"), torch.tensor(gd, device="cuda"), F)
+    Fo = sipg.rhs(m, lambda x: 3 * np.pi ** 2 * u_exact(x), gD_fun, 10.0)
+    assert rel_l2(F.cpu().numpy(), Fo) < 1e-12
+    # quadrature points are the oracle's physical GL points
+    e = m.n_elems - 1
+    pts = sipg.volume_points(m, e)
+    off = m.dof_off[e]
+    assert np.abs(vxyz[:, off:off + len(pts)].T.cpu().numpy() - pts).max() < 1e-13
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["config1_affine_p3", "mixed_curved_2to1_l1"])
+def test_smoother_fp64(name, torch):
+    from paper_1907_01572_gb300 import dgell
+    desc, m, H = hierarchy(name)
+    ctx = dgell.Context(desc)
+    for l in range(H.n_levels):
+        b = inputs.random_vector(H.meshes[l].n_dofs, seed=20 + l)
+        x0 = inputs.random_vector(H.meshes[l].n_dofs, seed=40 + l) * 0.1
+        xo, lam_o = multigrid.smoother(H.J[l], x0, b, 15, 15, 20.0)
+        xd = torch.tensor(x0, device="cuda")
+        lam = ctx.smooth(torch.tensor(b, device="cuda"), xd, level=l)
+        assert abs(lam - lam_o) <= 1e-10 * lam_o
+        assert rel_l2(xd.cpu().numpy(), xo) < 1e-10
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["config1_affine_p3", "mixed_curved_2to1_l1"])
+@pytest.mark.parametrize("coarse", [0, 1])
+def test_vcycle_fp64(name, coarse, torch):
+    from paper_1907_01572_gb300 import dgell
+    desc, m, H = hierarchy(name)
+    ctx = dgell.Context(desc)
+    f = inputs.random_vector(m.n_dofs, seed=3)
+    vo = H.vcycle(f, coarse='cholesky' if coarse else 'smoother')
+    v = torch.empty(m.n_dofs, dtype=torch.float64, device="cuda")
+    ctx.vcycle(torch.tensor(f, device="cuda"), v, coarse=coarse)
+    assert rel_l2(v.cpu().numpy(), vo) < 1e-9
+    # FP32 V-cycle stays close to the FP64 one
+    v32 = torch.empty(m.n_dofs, dtype=torch.float32, device="cuda")
+    ctx.vcycle(torch.tensor(f, device="cuda").float(), v32, coarse=coarse)
+    assert rel_l2(v32.double().cpu().numpy(), vo) < 1e-3
+    ctx.close()
+
+
+def test_poisson_solve_fp64_and_mixed(torch):
+    """Config-1 Poisson solve to 1e-10 relative residual: plain FP64 and FP32
+    V-cycle inside FP64 FCG; solution and discretisation error vs the oracle."""
+    from paper_1907_01572_gb300 import dgell
+    desc, m, H = hierarchy("config1_affine_p3")
+    Fo = sipg.rhs(m, lambda x: 3 * np.pi ** 2 * u_exact(x), u_exact, 10.0)
+    xo, it_o, _ = krylov.fcg(H.J[-1], Fo, precond=lambda r: H.vcycle(r), tol=1e-10)
+    err_o = sipg.l2_error(m, xo, u_exact)
+    ctx = dgell.Context(desc)
+    F = torch.tensor(Fo, device="cuda")
+    for prec in (dgell.DG_FP64, dgell.DG_FP32):
+        x = torch.zeros_like(F)
+        st = ctx.solve(F, x, tol=1e-10, max_iter=50, mg_prec=prec)
+        assert st["rel_residual"] < 1e-10, st
+        assert st["iterations"] <= it_o + (0 if prec == dgell.DG_FP64 else 3), (st, it_o)
+        xs = x.cpu().numpy()
+        assert rel_l2(xs, xo) < 1e-8
+        err = sipg.l2_error(m, xs, u_exact)
+        assert abs(err - err_o) <= 0.01 * err_o
+    # no preconditioner: CG iterates
+    x = torch.zeros_like(F)
+    st = ctx.solve(F, x, tol=1e-10, max_iter=1000, use_mg=0)
+    _, it_cg, _ = krylov.fcg(H.J[-1], Fo, tol=1e-10, max_iter=1000)
+    assert abs(st["iterations"] - it_cg) <= 2 and st["rel_residual"] < 1e-10
+    ctx.close()
+
+
+def test_solve_reports_not_converged(torch):
+    from paper_1907_01572_gb300 import dgell
+    desc, m, H = hierarchy("config1_affine_p3")
+    ctx = dgell.Context(desc)
+    F = torch.tensor(inputs.random_vector(m.n_dofs, seed=9), device="cuda")
+    x = torch.zeros_like(F)
+    st = ctx.solve(F, x, check=False, tol=1e-14, max_iter=2)
+    assert st["status"] == dgell.DG_ERR_NOT_CONVERGED and st["iterations"] == 2
+    ctx.close()
