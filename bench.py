@@ -170,9 +170,9 @@ def main():
     # CPU baseline first (own process, before any heavy GPU work)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        g, dofs, dt = cpu_baseline_sample(24, seed=0)
+        g, dofs, dt = cpu_baseline_sample(48, seed=0)
         cpu = {"value": g, "unit": "GDOF/s", "cores": 1, "kind": "oracle",
-               "sample": "24 random elements (%d DOFs, %.1f s) of the same mesh, dense-local FP64 apply "
+               "sample": "48 random elements (%d DOFs, %.1f s) of the same mesh, dense-local FP64 apply "
                          "incl. their mortars, single thread" % (dofs, dt)}
 
     import __graft_entry__
