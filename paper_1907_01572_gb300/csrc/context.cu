@@ -54,6 +54,8 @@ LevelView<double> view<double>(dg_ctx* c, int l) {
     v.mg = L.mg64;
     v.sigma = L.sigma64;
     v.tab = c->tab64;
+    v.ftab = c->ftab64;
+    v.ft = c->ft;
     return v;
 }
 
@@ -77,6 +79,8 @@ LevelView<float> view<float>(dg_ctx* c, int l) {
     v.mg = L.mg32;
     v.sigma = L.sigma32;
     v.tab = c->tab32;
+    v.ftab = c->ftab32;
+    v.ft = c->ft;
     return v;
 }
 
@@ -453,6 +457,11 @@ int dg_ctx_create(const dg_mesh_desc* mesh, const dg_disc_opts* opts, void* stre
     std::vector<float> tabf(tab.begin(), tab.end());
     c->tab64 = c->arena.upload(tab, c->st);
     c->tab32 = c->arena.upload(tabf, c->st);
+    std::vector<double> ftab;
+    build_face_tables(tab, ftab, c->ft);
+    std::vector<float> ftabf(ftab.begin(), ftab.end());
+    c->ftab64 = c->arena.upload(ftab, c->st);
+    c->ftab32 = c->arena.upload(ftabf, c->st);
     c->red.partials = c->arena.alloc<double>(kRedBlocks * 4);
     c->red.out = c->arena.alloc<double>(4);
     c->fcg = c->arena.alloc<FcgState>(1);

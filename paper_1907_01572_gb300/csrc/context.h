@@ -77,6 +77,9 @@ struct dg_ctx {
     dg::Arena arena;
     double* tab64 = nullptr;
     float* tab32 = nullptr;
+    double* ftab64 = nullptr;
+    float* ftab32 = nullptr;
+    dg::FaceTabs ft{};
     dg::Red red{};
     double* red_host = nullptr;     // pinned, 4 doubles
     dg::FcgState* fcg = nullptr;

@@ -142,4 +142,22 @@ void build_tables(std::vector<double>& tab) {
             }
 }
 
+void build_face_tables(const std::vector<double>& tab, std::vector<double>& ftab, FaceTabs& ft) {
+    ftab.clear();
+    for (int n = kMinN; n <= kMaxN; ++n)
+        for (int q = kMinN; q <= kMaxN; ++q)
+            for (int pos = 0; pos < 3; ++pos) {
+                if (q < n) {
+                    ft.off[n - kMinN][q - kMinN][pos] = -1;
+                    continue;
+                }
+                ft.off[n - kMinN][q - kMinN][pos] = (int)ftab.size();
+                const double* Im = &tab[tab_m(TabIndex::Im, n, q, pos)];
+                const double* Dm = &tab[tab_m(TabIndex::Dm, n, q, pos)];
+                ftab.insert(ftab.end(), Im, Im + q * n);
+                ftab.insert(ftab.end(), Dm, Dm + q * n);
+            }
+    ft.total = (int)ftab.size();
+}
+
 }  // namespace dg

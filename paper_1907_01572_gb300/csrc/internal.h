@@ -51,6 +51,15 @@ __host__ __device__ inline int tab_ci(int nH, int nh, int b) {
 
 void build_tables(std::vector<double>& tab);   // size TabIndex::Count * kTabStride
 
+// Compact mortar tables for the apply kernel's shared memory: for every side
+// degree n and mortar q >= n (q = max of both sides' n), sub-face pos 0..2,
+// the q x n matrices Im then Dm, packed without padding.
+struct FaceTabs {
+    int off[kNumN][kNumN][3];   // [n-2][q-2][pos] -> offset of Im (Dm follows at + q*n); -1 if q < n
+    int total;
+};
+void build_face_tables(const std::vector<double>& tab, std::vector<double>& ftab, FaceTabs& ft);
+
 // ---- mesh ----------------------------------------------------------------------
 struct Mortar {            // device record (32 bytes)
     int eA, eB;            // eA: geometry ('-') side = finer / lower index; eB = -1 on the boundary
@@ -110,6 +119,8 @@ struct LevelView {         // passed by value to kernels
     const T* mg;           // 7 * n_mortar_pts: [wS, cA0, cA1, cA2, cB0, cB1, cB2] blocks per mortar
     const T* sigma;        // per mortar
     const T* tab;
+    const T* ftab;         // compact mortar tables (FaceTabs layout)
+    FaceTabs ft;
 };
 
 struct DevBuf {
