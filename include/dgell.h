@@ -152,6 +152,23 @@ typedef struct {
 int dg_smooth(dg_ctx* ctx, int level, int prec, const void* b, void* x,
               const dg_cheb_opts* opts, double* lambda_max_out);
 
+/* dg_smooth without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc when they
+ * smooth (all free device memory already handed to a caching allocator or
+ * admitted to other work, or loops that cannot take cudaMalloc's implicit
+ * device synchronisation).  Same arguments, algorithm and results as
+ * dg_smooth, but its work vectors and reduction scratch live in one
+ * fixed-size array compiled into the library (about 6 MB, reserved on every
+ * GPU that loads the library until the process exits), so the level must have
+ * at most 262,144 DOFs (larger levels: DG_ERR_INVALID).  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, that
+ * device current): make it before any stream capture.  All calls share the
+ * array and it keeps the previous call's contents (the call clears what must
+ * start at zero); calls whose GPU work overlaps -- other streams, other
+ * threads -- race on it. */
+int dg_smooth_static(dg_ctx* ctx, int level, int prec, const void* b, void* x,
+                     const dg_cheb_opts* opts, double* lambda_max_out);
+
 /* Multigrid V-cycle (Alg. 3) as a preconditioner: v = VCYCLE(f) on the
  * finest level, starting from v = 0 on every level, pre- and post-smoothing
  * with dg_smooth's smoother, restriction = transpose of the prolongation

@@ -86,6 +86,7 @@ _SIGS = {
     "dg_convert": ([_P, ctypes.c_int64, ctypes.c_int, _P, ctypes.c_int, _P], ctypes.c_int),
     "dg_launch_count": ([_P], ctypes.c_int64),
     "dg_transfer": ([_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P], ctypes.c_int),
+    "dg_smooth_static": ([_P, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.POINTER(dg_cheb_opts), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
 }
 
 _lib = None
@@ -237,6 +238,14 @@ class Context:
         lam = ctypes.c_double(0.0)
         _check(lib().dg_smooth(self.h, level, _prec(b), _ptr(b), _ptr(x), ctypes.byref(o),
                                ctypes.byref(lam) if want_lambda else None))
+        return lam.value
+
+    def smooth_static(self, b, x, level=-1, n_eigs=15, n_cheb=15, Lambda=20.0, want_lambda=True):
+        """dg_smooth on the library's fixed scratch array (no device allocation)."""
+        o = cheb_opts(n_eigs, n_cheb, Lambda)
+        lam = ctypes.c_double(0.0)
+        _check(lib().dg_smooth_static(self.h, level, _prec(b), _ptr(b), _ptr(x), ctypes.byref(o),
+                                      ctypes.byref(lam) if want_lambda else None))
         return lam.value
 
     def vcycle(self, f, v, **mg):
