@@ -21,19 +21,28 @@
 // per bucket computes y with no intermediate buffers.
 //
 // Execution: one warp per element (lanes own pencils of the n^3 tensor grid,
-// __syncwarp between phases, no CTA-wide barrier after the table load);
-// persistent CTAs stride over the bucket; all 1-D tables, including every
-// mortar interpolation / derivative table, sit in shared memory.
+// __syncwarp between phases, no CTA-wide barrier after the table load); one
+// persistent CTA per SM strides over the bucket with as many warps as shared
+// memory and registers allow; all 1-D tables (FP32: also every mortar
+// interpolation / derivative table) sit in shared memory.
+#pragma once
 #include "apply.h"
 
 namespace dg {
-namespace {
+namespace apply_detail {
 
 constexpr int kQ = kMaxN;  // largest mortar q and neighbour n
 
 __device__ inline void tangential(int d, int& t1, int& t2) {
     t1 = d == 0 ? 1 : 0;
     t2 = d == 2 ? 1 : 2;
+}
+
+// k -> (k % q, k / q) for the small runtime sizes of the face phase (k < 1024,
+// q <= 9): float reciprocal, exact in this range, much cheaper than an integer divide.
+__device__ __forceinline__ void split(int k, int q, float qinv, int& r, int& s) {
+    s = __float2int_rz((k + 0.5f) * qinv);
+    r = k - s * q;
 }
 
 // out = M in along direction DIR of an N^3 array held by one warp (TRANS: M^T; ACC: out +=).
@@ -161,7 +170,9 @@ __global__ void apply_kernel(LevelView<T> L, const int* __restrict__ bucket, int
         __syncwarp();
         wpass<N, 2, true, false>(B, Y, sI, lane);
         __syncwarp();
-        if (L.Ob != nullptr) {
+        if (L.Ob != nullptr && L.Ob_off[e] + (long long)N3 * N3 > L.ob_total) {
+            if (lane == 0) atomicExch(L.chk, 1);
+        } else if (L.Ob != nullptr) {
             const T* Oe = L.Ob + L.Ob_off[e];
             for (int k = lane; k < N3; k += 32) {
                 T s = 0;
@@ -172,17 +183,25 @@ __global__ void apply_kernel(LevelView<T> L, const int* __restrict__ bucket, int
         }
         // ---- faces ----------------------------------------------------------------------
         const int s0 = L.slot_off[e], s1 = L.slot_off[e + 1];
+        int mi_next = L.slot_mortar[s0];
+        Mortar M_next = L.mortars[mi_next];
         for (int si = s0; si < s1; ++si) {
-            const int mi = L.slot_mortar[si];
+            const int mi = mi_next;
+            const Mortar M = M_next;
+            if (si + 1 < s1) {   // prefetch the next slot's mortar record
+                mi_next = L.slot_mortar[si + 1];
+                M_next = L.mortars[mi_next];
+            }
             const int f = L.slot_face[si];
             const int side = L.slot_side[si];
-            const Mortar M = L.mortars[mi];
             const int q = M.q, q2 = q * q;
+            const float qinv = 1.0f / (float)q;
             const T sig = L.sigma[mi];
             int p0, p1, eo, fo, o0, o1;
             if (side == 0) { p0 = M.posA0; p1 = M.posA1; eo = M.eB; fo = M.fB; o0 = M.posB0; o1 = M.posB1; }
             else { p0 = M.posB0; p1 = M.posB1; eo = M.eA; fo = M.fA; o0 = M.posA0; o1 = M.posA1; }
             const int nbN = eo >= 0 ? L.p[eo] + 1 : 2;
+            const float nbinv = 1.0f / (float)nbN;
             const int d = f >> 1, fn = (f & 1) ? N - 1 : 0;
             int t1, t2;
             tangential(d, t1, t2);
@@ -202,7 +221,8 @@ __global__ void apply_kernel(LevelView<T> L, const int* __restrict__ bucket, int
                 const int fno = (fo & 1) ? nbN - 1 : 0;
                 const T* DLn = L.tab + tab_n(TabIndex::DL, nbN) + fno * nbN;
                 for (int k = lane; k < nbN * nbN; k += 32) {
-                    const int a = k % nbN, b = k / nbN;
+                    int a, b;
+                    split(k, nbN, nbinv, a, b);
                     const int base = a * nst[t1] + b * nst[t2];
                     T acc = 0, fv = 0;
                     for (int c = 0; c < nbN; ++c) {
@@ -221,7 +241,8 @@ __global__ void apply_kernel(LevelView<T> L, const int* __restrict__ bucket, int
             const T* Dm2 = Im2 + q * N;
             // S2: interpolate along the first tangential axis
             for (int k = lane; k < q * N; k += 32) {
-                const int i1 = k % q, b = k / q;
+                int i1, b;
+                split(k, q, qinv, i1, b);
                 T su = 0, sd = 0, sn = 0;
 #pragma unroll
                 for (int a = 0; a < N; ++a) {
@@ -242,7 +263,8 @@ __global__ void apply_kernel(LevelView<T> L, const int* __restrict__ bucket, int
                 Im2n = sFT + L.ft.off[nbN - kMinN][q - kMinN][o1];
                 const T* Dm1n = Im1n + q * nbN;
                 for (int k = lane; k < q * nbN; k += 32) {
-                    const int i1 = k % q, b = k / q;
+                    int i1, b;
+                split(k, q, qinv, i1, b);
                     T su = 0, sd = 0, sn = 0;
                     for (int a = 0; a < nbN; ++a) {
                         const T iv = Im1n[i1 * nbN + a], dv = Dm1n[i1 * nbN + a];
@@ -263,7 +285,8 @@ __global__ void apply_kernel(LevelView<T> L, const int* __restrict__ bucket, int
                 const T sgn = side == 0 ? T(1) : T(-1);
                 const int oo = side == 0 ? 1 : 4, on = side == 0 ? 4 : 1;
                 for (int k = lane; k < q2; k += 32) {
-                    const int i1 = k % q, i2 = k / q;
+                    int i1, i2;
+                split(k, q, qinv, i1, i2);
                     T u = 0, gt1 = 0, gt2 = 0, gn = 0;
 #pragma unroll
                     for (int b = 0; b < N; ++b) {
@@ -309,7 +332,8 @@ __global__ void apply_kernel(LevelView<T> L, const int* __restrict__ bucket, int
             __syncwarp();
             // S4: transposed interpolation along the second tangential axis
             for (int k = lane; k < q * N; k += 32) {
-                const int i1 = k % q, b = k / q;
+                int i1, b;
+                split(k, q, qinv, i1, b);
                 T s1v = 0, s2v = 0, s3v = 0;
                 for (int i2 = 0; i2 < q; ++i2) {
                     const T iv = Im2[i2 * N + b], dv = Dm2[i2 * N + b];
@@ -343,37 +367,50 @@ __global__ void apply_kernel(LevelView<T> L, const int* __restrict__ bucket, int
     }
 }
 
-int g_sm_count = 0;
+inline int& sm_count() {
+    static int v = 0;
+    return v;
+}
 
 template <int N, typename T>
 cudaError_t launch_n(const LevelView<T>& L, const BucketInfo& b, const T* x, T* y, cudaStream_t st) {
     using Ly = Layout<N>;
-    const size_t table_vals = (sizeof(T) == 4 ? ((L.ft.total + 3) & ~3) : 0) + 3 * N * N;
-    const size_t budget = 100 * 1024;
-    int W = 8;
-    while (W > 1 && (table_vals + (size_t)W * Ly::WARP) * sizeof(T) > budget) --W;
-    const size_t smem = (table_vals + (size_t)W * Ly::WARP) * sizeof(T);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t err = cudaFuncSetAttribute(apply_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    static int W = 0;
+    static size_t smem = 0;
+    if (W == 0) {
+        // one persistent CTA per SM; warps limited by shared memory (tables staged once per CTA)
+        // and by the register file
+        const size_t table_vals = (sizeof(T) == 4 ? ((L.ft.total + 3) & ~3) : 0) + 3 * N * N;
+        const size_t cap = 220 * 1024;
+        cudaError_t err = cudaFuncSetAttribute(apply_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)cap);
         if (err != cudaSuccess) return err;
-        attr_set = true;
+        int w = (int)((cap - table_vals * sizeof(T)) / (Ly::WARP * sizeof(T)));
+        if (w > 24) w = 24;
+        for (; w > 1; --w) {   // largest warp count of which one CTA fits on an SM
+            const size_t sm_bytes = (table_vals + (size_t)w * Ly::WARP) * sizeof(T);
+            int blocks = 0;
+            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, apply_kernel<N, T>, w * 32, sm_bytes);
+            if (err != cudaSuccess) return err;
+            if (blocks >= 1) break;
+        }
+        W = w;
+        smem = (table_vals + (size_t)W * Ly::WARP) * sizeof(T);
     }
+    int& g_sm_count = sm_count();
     if (g_sm_count == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
         if (g_sm_count <= 0) g_sm_count = 152;
     }
-    const int per_sm = (int)((227 * 1024) / (smem + 1024));
-    const int max_grid = g_sm_count * (per_sm < 1 ? 1 : per_sm);
     int grid = (b.count + W - 1) / W;
-    if (grid > max_grid) grid = max_grid;
+    if (grid > g_sm_count) grid = g_sm_count;
     apply_kernel<N, T><<<grid, W * 32, smem, st>>>(L, b.elems, b.count, x, y);
     return cudaGetLastError();
 }
 
-}  // namespace
+}  // namespace apply_detail
 
 template <typename T>
 cudaError_t launch_apply(const LevelView<T>& L, const BucketInfo* buckets, const T* x, T* y, cudaStream_t st,
@@ -383,24 +420,19 @@ cudaError_t launch_apply(const LevelView<T>& L, const BucketInfo* buckets, const
         if (b.count == 0) continue;
         cudaError_t err = cudaSuccess;
         switch (n) {
-            case 2: err = launch_n<2, T>(L, b, x, y, st); break;
-            case 3: err = launch_n<3, T>(L, b, x, y, st); break;
-            case 4: err = launch_n<4, T>(L, b, x, y, st); break;
-            case 5: err = launch_n<5, T>(L, b, x, y, st); break;
-            case 6: err = launch_n<6, T>(L, b, x, y, st); break;
-            case 7: err = launch_n<7, T>(L, b, x, y, st); break;
-            case 8: err = launch_n<8, T>(L, b, x, y, st); break;
-            case 9: err = launch_n<9, T>(L, b, x, y, st); break;
+            case 2: err = apply_detail::launch_n<2, T>(L, b, x, y, st); break;
+            case 3: err = apply_detail::launch_n<3, T>(L, b, x, y, st); break;
+            case 4: err = apply_detail::launch_n<4, T>(L, b, x, y, st); break;
+            case 5: err = apply_detail::launch_n<5, T>(L, b, x, y, st); break;
+            case 6: err = apply_detail::launch_n<6, T>(L, b, x, y, st); break;
+            case 7: err = apply_detail::launch_n<7, T>(L, b, x, y, st); break;
+            case 8: err = apply_detail::launch_n<8, T>(L, b, x, y, st); break;
+            case 9: err = apply_detail::launch_n<9, T>(L, b, x, y, st); break;
         }
         if (err != cudaSuccess) return err;
         if (launches) ++*launches;
     }
     return cudaSuccess;
 }
-
-template cudaError_t launch_apply<double>(const LevelView<double>&, const BucketInfo*, const double*, double*,
-                                          cudaStream_t, int*);
-template cudaError_t launch_apply<float>(const LevelView<float>&, const BucketInfo*, const float*, float*,
-                                         cudaStream_t, int*);
 
 }  // namespace dg

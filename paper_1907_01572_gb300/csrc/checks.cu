@@ -1,0 +1,40 @@
+// Self-check flag shared by the kernels that index through offset tables, and
+// the DGELL_DEBUG_SYNC switch (synchronise after every checked launch and
+// report the launch by name).
+#include <cstdlib>
+#include <mutex>
+
+#include "internal.h"
+
+namespace dg {
+namespace {
+__device__ int g_check_flag_dev;
+std::mutex g_mu;
+int* g_flag_addr[64] = {};
+}  // namespace
+
+int* device_check_flag() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_flag_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_check_flag_dev) == cudaSuccess) {
+            g_flag_addr[dev] = static_cast<int*>(p);
+            cudaMemset(p, 0, sizeof(int));
+        }
+    }
+    return g_flag_addr[dev];
+}
+
+bool debug_sync() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = std::getenv("DGELL_DEBUG_SYNC");
+        v = (e && e[0] == '1') ? 1 : 0;
+    }
+    return v == 1;
+}
+
+}  // namespace dg

@@ -23,7 +23,13 @@ int fail(int code, const std::string& msg) {
 #define CK(call)                                                                         \
     do {                                                                                 \
         cudaError_t _e = (call);                                                         \
+        if (_e == cudaSuccess && debug_sync()) _e = cudaDeviceSynchronize();             \
         if (_e != cudaSuccess) return fail(DG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
+        if (debug_sync()) {                                                              \
+            int _f = 0;                                                                  \
+            cudaMemcpy(&_f, device_check_flag(), sizeof(int), cudaMemcpyDeviceToHost);  \
+            if (_f) return fail(DG_ERR_CUDA, "self-check " + std::to_string(_f) + " in " + #call); \
+        }                                                                                \
     } while (0)
 
 int resolve_level(dg_ctx* c, int level) {
@@ -43,8 +49,8 @@ LevelView<double> view<double>(dg_ctx* c, int l) {
     v.dof_off = L.dof_off;
     v.vqp_off = L.vqp_off;
     v.G = L.G64;
-    v.c0 = L.c0_64;
-    v.Ob = L.Ob64;
+    v.c0 = L.z_active ? L.c0_64 : nullptr;
+    v.Ob = L.z_active ? L.Ob64 : nullptr;
     v.Ob_off = L.Ob_off;
     v.slot_off = L.slot_off;
     v.slot_mortar = L.slot_mortar;
@@ -56,6 +62,8 @@ LevelView<double> view<double>(dg_ctx* c, int l) {
     v.tab = c->tab64;
     v.ftab = c->ftab64;
     v.ft = c->ft;
+    v.ob_total = (long long)L.ob_count;
+    v.chk = device_check_flag();
     return v;
 }
 
@@ -68,8 +76,8 @@ LevelView<float> view<float>(dg_ctx* c, int l) {
     v.dof_off = L.dof_off;
     v.vqp_off = L.vqp_off;
     v.G = L.G32;
-    v.c0 = L.c0_32;
-    v.Ob = L.Ob32;
+    v.c0 = L.z_active ? L.c0_32 : nullptr;
+    v.Ob = L.z_active ? L.Ob32 : nullptr;
     v.Ob_off = L.Ob_off;
     v.slot_off = L.slot_off;
     v.slot_mortar = L.slot_mortar;
@@ -81,6 +89,8 @@ LevelView<float> view<float>(dg_ctx* c, int l) {
     v.tab = c->tab32;
     v.ftab = c->ftab32;
     v.ft = c->ft;
+    v.ob_total = (long long)L.ob_count;
+    v.chk = device_check_flag();
     return v;
 }
 

@@ -60,6 +60,11 @@ struct LevelDev {
     double* Ob64 = nullptr;
     float* Ob32 = nullptr;
     long long* Ob_off = nullptr;
+    bool z_active = false;            // zeroth-order term (c0 on the finest level, Ob on coarse levels) in use
+    // Galerkin structure of a coarse level: finest descendants and their reference maps
+    int *g_desc_off = nullptr, *g_desc = nullptr;
+    double* g_map = nullptr;
+    size_t ob_count = 0;
     // transfer to the next finer level (this level is the coarse side)
     int *child_off = nullptr, *child_id = nullptr, *fine_parent = nullptr;
     unsigned char *child_bits = nullptr, *fine_bits = nullptr;
@@ -92,5 +97,7 @@ struct dg_ctx {
     // puncture data on the finest level volume points
     double* p_alpha = nullptr;
     double* p_beta = nullptr;
+    double* nw[4] = {};             // Newton work vectors (double, finest): R, du, Lu, S
+    bool galerkin_ready = false;
     long long launches = 0;
 };

@@ -121,7 +121,14 @@ struct LevelView {         // passed by value to kernels
     const T* tab;
     const T* ftab;         // compact mortar tables (FaceTabs layout)
     FaceTabs ft;
+    long long ob_total;    // entries of Ob (bounds check)
+    int* chk;              // self-check flag
 };
+
+// Self-check support: kernels that index with offsets read from tables check
+// them against the buffer sizes, skip the access and record a code here.
+int* device_check_flag();          // device pointer to one int (0 = ok)
+bool debug_sync();                 // DGELL_DEBUG_SYNC=1: synchronise and name every checked launch
 
 struct DevBuf {
     void* ptr = nullptr;

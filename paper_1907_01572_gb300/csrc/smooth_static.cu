@@ -72,22 +72,24 @@ LevelView<T> static_view(dg_ctx* c, int l) {
     v.mortars = L.mortars;
     if constexpr (sizeof(T) == 8) {
         v.G = (const T*)L.G64;
-        v.c0 = (const T*)L.c0_64;
-        v.Ob = (const T*)L.Ob64;
+        v.c0 = L.z_active ? (const T*)L.c0_64 : nullptr;
+        v.Ob = L.z_active ? (const T*)L.Ob64 : nullptr;
         v.mg = (const T*)L.mg64;
         v.sigma = (const T*)L.sigma64;
         v.tab = (const T*)c->tab64;
         v.ftab = (const T*)c->ftab64;
     } else {
         v.G = (const T*)L.G32;
-        v.c0 = (const T*)L.c0_32;
-        v.Ob = (const T*)L.Ob32;
+        v.c0 = L.z_active ? (const T*)L.c0_32 : nullptr;
+        v.Ob = L.z_active ? (const T*)L.Ob32 : nullptr;
         v.mg = (const T*)L.mg32;
         v.sigma = (const T*)L.sigma32;
         v.tab = (const T*)c->tab32;
         v.ftab = (const T*)c->ftab32;
     }
     v.ft = c->ft;
+    v.ob_total = (long long)L.ob_count;
+    v.chk = device_check_flag();
     return v;
 }
 

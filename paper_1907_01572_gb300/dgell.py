@@ -285,11 +285,12 @@ class Context:
         _check(lib().dg_newton_step(self.h, _ptr(u), ctypes.byref(o), ctypes.byref(s), ctypes.byref(rn)))
         return rn.value, {k: getattr(s, k) for k, _ in dg_solve_stats._fields_}
 
-    def newton_solve(self, u, tol=1e-10, max_newton=20, **kw):
+    def newton_solve(self, u, tol_newton=1e-10, max_newton=20, **kw):
+        """Alg. 1; kw are the linear solver's options (tol, max_iter, mg_prec, ...)."""
         o = solver_opts(**kw)
         steps = ctypes.c_int(0)
         rn = ctypes.c_double(0.0)
-        _check(lib().dg_newton_solve(self.h, _ptr(u), tol, max_newton, ctypes.byref(o), ctypes.byref(steps),
+        _check(lib().dg_newton_solve(self.h, _ptr(u), tol_newton, max_newton, ctypes.byref(o), ctypes.byref(steps),
                                      ctypes.byref(rn)))
         return steps.value, rn.value
 

@@ -1,0 +1,114 @@
+"""GPU parity of the zeroth-order term (eq. lh2) with its Galerkin coarse-level
+form O^H = I^T O^h I (eq. operator_oh), the puncture residual (Sec. III.D) and
+Newton-Raphson (Alg. 1) against the oracle."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from gpu_util import CASES, oracle_mesh, rel_l2
+from oracle import multigrid, puncture, sipg
+from oracle.mesh import Mesh
+from paper_1907_01572_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+PUNC = [(0.5, (3.0, 0.1, 0.05), (0.0, 0.2, 0.0)), (0.5, (-3.0, 0.1, 0.05), (0.0, -0.2, 0.0))]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def coef_fun(x):
+    return 1.0 + x[:, 0] ** 2 + 0.5 * np.sin(x[:, 1])
+
+
+@pytest.mark.parametrize("name", ["config1_affine_p3", "mixed_curved_2to1_l1"])
+def test_zeroth_order_and_galerkin_levels(name):
+    import torch
+    from paper_1907_01572_gb300 import dgell
+    desc = CASES[name]()
+    m = oracle_mesh(desc)
+    coef = [coef_fun(sipg.volume_points(m, e)) for e in range(m.n_elems)]
+    H = multigrid.Hierarchy(m, coef=coef)
+    ctx = dgell.Context(desc)
+    vxyz, _ = ctx.quadrature_points()
+    ctx.set_zeroth_order(torch.tensor(coef_fun(vxyz.T.cpu().numpy()), device="cuda"))
+    for l in range(H.n_levels):
+        x = inputs.random_vector(H.meshes[l].n_dofs, seed=60 + l)
+        y = torch.empty(H.meshes[l].n_dofs, dtype=torch.float64, device="cuda")
+        ctx.apply(torch.tensor(x, device="cuda"), y, level=l)
+        assert rel_l2(y.cpu().numpy(), H.J[l] @ x) < 1e-12, l
+        y32 = torch.empty(H.meshes[l].n_dofs, dtype=torch.float32, device="cuda")
+        x32 = torch.tensor(x, device="cuda").float()
+        ctx.apply(x32, y32, level=l)
+        assert rel_l2(y32.double().cpu().numpy(), H.J[l] @ x32.double().cpu().numpy()) < 1e-5, l
+    # clearing the term restores the Laplacian
+    ctx.set_zeroth_order(None)
+    x = inputs.random_vector(m.n_dofs, seed=70)
+    y = torch.empty(m.n_dofs, dtype=torch.float64, device="cuda")
+    ctx.apply(torch.tensor(x, device="cuda"), y)
+    assert rel_l2(y.cpu().numpy(), H.L[-1] @ x) < 1e-12
+    ctx.close()
+
+
+def _puncture_mesh(level=2, p=3):
+    lv = inputs.uniform_leaves(level)
+    return dict(lo=(-6.0, -6.0, -6.0), hi=(6.0, 6.0, 6.0), leaves=np.array(lv, dtype=np.int32),
+                p=np.full(len(lv), p, dtype=np.int32), warp=None)
+
+
+def test_puncture_residual():
+    import torch
+    from paper_1907_01572_gb300 import dgell
+    desc = _puncture_mesh(level=1, p=4)
+    m = Mesh(desc["lo"], desc["hi"], desc["leaves"], desc["p"])
+    prob = puncture.PunctureProblem(m, PUNC)
+    u = 0.05 * inputs.random_vector(m.n_dofs, seed=5)
+    ctx = dgell.Context(desc)
+    ctx.puncture_setup(PUNC)
+    R = torch.empty(m.n_dofs, dtype=torch.float64, device="cuda")
+    ctx.puncture_residual(torch.tensor(u, device="cuda"), R)
+    assert rel_l2(R.cpu().numpy(), prob.residual(u)) < 1e-12
+    ctx.close()
+
+
+def test_newton_solve_matches_oracle():
+    import torch
+    from paper_1907_01572_gb300 import dgell
+    desc = _puncture_mesh(level=2, p=3)
+    m = Mesh(desc["lo"], desc["hi"], desc["leaves"], desc["p"])
+    prob = puncture.PunctureProblem(m, PUNC)
+
+    def ls(coef, rhs):
+        return spla.spsolve(sipg.assemble(m, 10.0, coef=coef).tocsc(), rhs)
+
+    uo, ko, hist = puncture.newton(prob, np.zeros(m.n_dofs), ls, tol=1e-12)
+    ctx = dgell.Context(desc)
+    ctx.puncture_setup(PUNC)
+    for prec in (dgell.DG_FP64, dgell.DG_FP32):
+        u = torch.zeros(m.n_dofs, dtype=torch.float64, device="cuda")
+        steps, rn = ctx.newton_solve(u, tol_newton=1e-10 * hist[0], max_newton=10, mg_prec=prec, tol=1e-11)
+        assert rn < 1e-10 * hist[0] and steps <= ko + 2, (steps, rn, hist)
+        assert rel_l2(u.cpu().numpy(), uo) < 1e-8
+    ctx.close()
+
+
+def test_newton_step_first_call_and_guards():
+    """A Newton step as the first call on a fresh context, and the error for a
+    Newton call before dg_puncture_setup."""
+    import torch
+    from paper_1907_01572_gb300 import dgell
+    desc = _puncture_mesh(level=1, p=3)
+    ctx = dgell.Context(desc)
+    u = torch.zeros(ctx.level_info()["n_dofs"], dtype=torch.float64, device="cuda")
+    with pytest.raises(dgell.DgError) as e:
+        ctx.newton_step(u)
+    assert e.value.code == dgell.DG_ERR_INVALID
+    ctx.puncture_setup(PUNC)
+    r0, st = ctx.newton_step(u, tol=1e-12)
+    r1, _ = ctx.newton_step(u, tol=1e-12)
+    assert r0 > 0 and r1 < 1e-2 * r0 and st["rel_residual"] < 1e-11
+    ctx.close()
