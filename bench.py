@@ -243,8 +243,10 @@ def main():
     ach64 = N * b64 / (ms64 * 1e-3) / 1e9
 
     solve = None
+    peaks_alu = alu_peaks(torch) if rank == 0 else {}
     if not args.no_solve and rank == 0:
         solve = solve_bench(dgell, inputs, torch)
+    flops = info["apply_flops"]
 
     if rank == 0:
         line = {
@@ -261,7 +263,15 @@ def main():
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
             "fp64": {"value": g64, "unit": "GDOF/s", "ms_per_step": ms64, "achieved_gbs": ach64,
-                     "bytes_per_dof": b64},
+                     "bytes_per_dof": b64,
+                     "roofline": {"bound": "alu", "achieved": flops / (ms64 * 1e-3) / 1e12,
+                                  "peak": peaks_alu.get("fp64"), "unit": "TFLOP/s",
+                                  "frac": (flops / (ms64 * 1e-3) / 1e12) / peaks_alu["fp64"] if peaks_alu else None,
+                                  "peak_kind": "measured this run: cuBLAS DGEMM 4096^3"}},
+            "fp32_alu": {"achieved": flops / (ms32 * 1e-3) / 1e12, "peak": peaks_alu.get("fp32"), "unit": "TFLOP/s",
+                         "frac": (flops / (ms32 * 1e-3) / 1e12) / peaks_alu["fp32"] if peaks_alu else None,
+                         "peak_kind": "measured this run: cuBLAS SGEMM 8192^3, TF32 off",
+                         "flops_per_apply": flops},
             "solve": solve,
         }
         print(json.dumps(line))
@@ -271,37 +281,101 @@ def main():
     return 0
 
 
+def _latency(lat):
+    lat = sorted(lat)
+    return {"solves_per_s": len(lat) / sum(lat), "p50_ms": 1e3 * lat[len(lat) // 2],
+            "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
+
+
 def solve_bench(dgell, inputs, torch, n_solves=8):
-    """Poisson -Lap u = 3 pi^2 sin sin sin on 4^3 elements, p = 3, MG-FCG to 1e-10."""
+    """Linear solves to 1e-10 relative residual (FP64 outer FCG) with the plain
+    FP64 V-cycle and with the FP32 V-cycle, each V-cycle replayed as a CUDA graph
+    on a dedicated stream: the 4^3 p=3 Poisson problem and the star with a
+    density jump (closed-form Dirichlet data); then the two-puncture Newton solve."""
     import numpy as np
-    desc = inputs.config1_mesh()
-    ctx = dgell.Context(desc)
-    xyz, bxyz = ctx.quadrature_points()
-    g = 3 * np.pi ** 2 * torch.sin(np.pi * xyz[0]) * torch.sin(np.pi * xyz[1]) * torch.sin(np.pi * xyz[2])
-    N = ctx.level_info()["n_dofs"]
-    F = torch.empty(N, dtype=torch.float64, device="cuda")
-    ctx.rhs(g.contiguous(), None, F)
     out = {}
-    for name, prec in (("fp64", dgell.DG_FP64), ("mixed_fp32_vcycle", dgell.DG_FP32)):
-        lat, its, res = [], [], []
-        for s in range(n_solves + 2):
-            x = torch.zeros_like(F)
-            torch.cuda.synchronize()
-            t = time.perf_counter()
-            st = ctx.solve(F, x, tol=1e-10, max_iter=100, mg_prec=prec)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t
-            if s >= 2:
-                lat.append(dt)
-                its.append(st["iterations"])
-                res.append(st["rel_residual"])
-        lat.sort()
-        out[name] = {"solves_per_s": len(lat) / sum(lat), "p50_ms": 1e3 * lat[len(lat) // 2],
-                     "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))], "iterations": its[-1],
-                     "max_rel_residual": max(res)}
-    ctx.close()
-    out["workload"] = "Poisson 4x4x4 affine hex, p=3 (4096 DOFs), manufactured sin solution, tol 1e-10"
+    stream = torch.cuda.Stream()
+    cases = [
+        ("poisson_4x4x4_p3", inputs.config1_mesh(),
+         lambda X: 3 * np.pi ** 2 * np.sin(np.pi * X[:, 0]) * np.sin(np.pi * X[:, 1]) * np.sin(np.pi * X[:, 2]),
+         None),
+        ("star_density_jump", inputs.star_mesh(), inputs.star_source, inputs.star_solution),
+    ]
+    with torch.cuda.stream(stream):
+        for name, desc, g, gD in cases:
+            ctx = dgell.Context(desc)
+            info = ctx.level_info()
+            xyz, bxyz = ctx.quadrature_points()
+            gq = torch.tensor(g(xyz.T.cpu().numpy()), device="cuda")
+            gd = torch.tensor(gD(bxyz.T.cpu().numpy()), device="cuda") if gD is not None else None
+            F = torch.empty(info["n_dofs"], dtype=torch.float64, device="cuda")
+            ctx.rhs(gq, gd, F)
+            res = {"n_dofs": info["n_dofs"], "n_elems": info["n_elems"], "levels": info["n_levels"]}
+            for pname, prec in (("fp64", dgell.DG_FP64), ("mixed_fp32_vcycle", dgell.DG_FP32)):
+                lat, its, rr = [], [], []
+                for s in range(n_solves + 2):
+                    x = torch.zeros_like(F)
+                    stream.synchronize()
+                    t = time.perf_counter()
+                    st = ctx.solve(F, x, tol=1e-10, max_iter=300, mg_prec=prec)
+                    stream.synchronize()
+                    dt = time.perf_counter() - t
+                    if s >= 2:
+                        lat.append(dt)
+                        its.append(st["iterations"])
+                        rr.append(st["rel_residual"])
+                r = _latency(lat)
+                r.update({"iterations": its[-1], "max_rel_residual": max(rr)})
+                res[pname] = r
+            out[name] = res
+            ctx.close()
+        # puncture Newton
+        punc = inputs.two_punctures()
+        desc = inputs.puncture_mesh(punc)
+        ctx = dgell.Context(desc)
+        info = ctx.level_info()
+        ctx.puncture_setup(punc)
+        res = {"n_dofs": info["n_dofs"], "n_elems": info["n_elems"], "levels": info["n_levels"]}
+        for pname, prec in (("fp64", dgell.DG_FP64), ("mixed_fp32_vcycle", dgell.DG_FP32)):
+            lat = []
+            for s in range(3):
+                u = torch.zeros(info["n_dofs"], dtype=torch.float64, device="cuda")
+                stream.synchronize()
+                t = time.perf_counter()
+                steps, rn = ctx.newton_solve(u, tol_newton=1e-9, max_newton=12, mg_prec=prec, tol=1e-10)
+                stream.synchronize()
+                lat.append(time.perf_counter() - t)
+            r = _latency(lat[1:])
+            r.update({"newton_steps": steps, "final_residual_norm": rn})
+            res[pname] = r
+        out["two_puncture_newton"] = res
+        ctx.close()
+    stream.synchronize()
     return out
+
+
+def alu_peaks(torch):
+    """Measured dense FP64 and FP32 (CUDA-core, TF32 off) GEMM rates in TFLOP/s."""
+    res = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    for name, dt, n in (("fp64", torch.float64, 4096), ("fp32", torch.float32, 8192)):
+        a = torch.randn(n, n, dtype=dt, device="cuda")
+        b = torch.randn(n, n, dtype=dt, device="cuda")
+        best = 1e9
+        for _ in range(3):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) * 1e-3)
+        res[name] = 2.0 * n ** 3 / best / 1e12
+        del a, b
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    return res
 
 
 if __name__ == "__main__":

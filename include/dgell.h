@@ -91,6 +91,9 @@ typedef struct {
     int n_mortars;
     int max_p;
     size_t device_bytes;   /* device memory held by the whole context */
+    double apply_flops;    /* floating-point operations of one dg_apply on the level
+                              (sum factorisation: 24 n^4 + 18 n^3 per element volume,
+                              per mortar side 4 n^3 + 12 q n^2 + 16 q^2 n + 20 q^2) */
 } dg_level_info;
 
 int dg_version(void);
@@ -193,6 +196,8 @@ typedef struct {
     int mg_prec;       /* precision of the V-cycle: DG_FP64 or DG_FP32 */
     int use_mg;        /* 0: no preconditioner (plain CG iterates) */
     dg_mg_opts mg;
+    int graph_mode;    /* 0: after one eager V-cycle, capture it once as a CUDA graph and
+                          replay it (needs a non-default stream); 1: always launch eagerly */
 } dg_solver_opts;
 
 typedef struct {

@@ -1,48 +1,43 @@
-// Matrix-free SIPG operator apply (eq. lh2), one fused element-centric kernel
+// Matrix-free SIPG operator apply (eq. lh2) in two element-centric kernels
 // per polynomial-degree bucket.
 //
+// Trace kernel: for every mortar touching the element (Sec. II.A.5, mortar
+// figure), the element's own trace u and normal derivative n_A . grad u at the
+// mortar's p_m + 1 GL points per direction: the face values and the face-normal
+// LGL derivative are interpolated with the sub-face / degree-change tables and
+// contracted with c = (J^-1) n_A of this side.  Written to the mortar trace
+// buffer MT (per mortar [u_A, dn_A, u_B, dn_B]).
+//
+// Element kernel (after all trace kernels of the level):
 // Volume (eq. harald-stiff), sum-factorised with 1-D operators (Sec. II.F.4):
 //   u~ = (I x I x I) u            values at the GL points         (3 passes)
 //   g_l = Dg_l u~                 reference gradient at GL points (3 passes)
 //   f_l = G_lm g_m                G = w det J J^-1 J^-T (stored)
 //   z = sum_l Dg_l^T f_l (+ c0 u~ for the zeroth-order term)     (3 passes)
 //   y = (I x I x I)^T z                                           (3 passes)
-// Faces (consistency, symmetry, penalty integrals of eq. lh2 with the hp
-// mortar projection of the mortar figure): for each mortar touching the
-// element, both sides' traces u and reference gradients are interpolated to
-// the mortar's GL points (sub-face tables for 2:1 faces, degree-change tables
-// for p-jumps); with n the element's outward normal,
-//   j = u_own - u_nb,  a = {n . grad u},
+// Faces (consistency, symmetry and penalty integrals of eq. lh2): with n the
+// element's outward normal (= sgn n_A) and both sides' traces from MT,
+//   j = u_own - u_nb,  a = {n . grad u} = sgn (dn_A + dn_B) / 2,
 //   y_alpha += sum_pts wS [ (sigma j - a) psi_alpha - (1/2) j n . grad psi_alpha ]
-// (on Dirichlet mortars j = u_own, a = n . grad u_own and the factor 1/2 is 1),
-// lifted back through the transposed interpolation and the face-normal row of
-// the LGL derivative matrix.  The neighbour's trace and normal derivative are
-// read straight from x (its element block, normally an L2 hit), so one launch
-// per bucket computes y with no intermediate buffers.
+// (Dirichlet mortars: j = u_own, a = n . grad u_own, factor 1 instead of 1/2),
+// lifted through the transposed mortar tables and the face-normal row of the
+// LGL derivative matrix.
 //
-// Execution: one warp per element (lanes own pencils of the n^3 tensor grid,
-// __syncwarp between phases, no CTA-wide barrier after the table load); one
-// persistent CTA per SM strides over the bucket with as many warps as shared
-// memory and registers allow; all 1-D tables (FP32: also every mortar
-// interpolation / derivative table) sit in shared memory.
+// Execution: one warp per element (lanes own pencils / face points, __syncwarp
+// between phases); persistent CTAs stride over the bucket, sized for the most
+// resident warps that shared memory and registers allow; face loops are
+// compiled per mortar size q; FP32 stages every mortar table in shared memory.
 #pragma once
 #include "apply.h"
 
 namespace dg {
 namespace apply_detail {
 
-constexpr int kQ = kMaxN;  // largest mortar q and neighbour n
+constexpr int kQ = kMaxN;  // largest mortar q
 
 __device__ inline void tangential(int d, int& t1, int& t2) {
     t1 = d == 0 ? 1 : 0;
     t2 = d == 2 ? 1 : 2;
-}
-
-// k -> (k % q, k / q) for the small runtime sizes of the face phase (k < 1024,
-// q <= 9): float reciprocal, exact in this range, much cheaper than an integer divide.
-__device__ __forceinline__ void split(int k, int q, float qinv, int& r, int& s) {
-    s = __float2int_rz((k + 0.5f) * qinv);
-    r = k - s * q;
 }
 
 // out = M in along direction DIR of an N^3 array held by one warp (TRANS: M^T; ACC: out +=).
@@ -67,40 +62,260 @@ __device__ inline void wpass(const T* __restrict__ in, T* __restrict__ out, cons
     }
 }
 
+template <typename T>
+struct SlotInfo {
+    int f, side, p0, p1, q;
+    long long goff;
+};
+
+template <typename T>
+__device__ __forceinline__ SlotInfo<T> slot_info(const LevelView<T>& L, int si) {
+    SlotInfo<T> s;
+    const Mortar M = L.mortars[L.slot_mortar[si]];
+    s.f = L.slot_face[si];
+    s.side = L.slot_side[si];
+    s.p0 = s.side == 0 ? M.posA0 : M.posB0;
+    s.p1 = s.side == 0 ? M.posA1 : M.posB1;
+    s.q = M.q;
+    s.goff = M.goff;
+    return s;
+}
+
+// Own trace at the Q x Q mortar points: u and dn = c^side . grad_xi u (c^side = J^-1 n_A).
+template <int N, int Q, typename T>
+__device__ __forceinline__ void trace_slot(const LevelView<T>& L, const SlotInfo<T>& s, const T* __restrict__ U,
+                                           const T* __restrict__ sDL, const T* __restrict__ sFT, T* F,
+                                           T* __restrict__ mt, int lane) {
+    if constexpr (Q < N) {
+        return;
+    } else {
+        constexpr int N2 = N * N, Q2 = Q * Q;
+        const int st[3] = {1, N, N2};
+        const int d = s.f >> 1, fn = (s.f & 1) ? N - 1 : 0;
+        int t1, t2;
+        tangential(d, t1, t2);
+        T* uf = F;
+        T* df = uf + N2;
+        T* U1 = df + N2;
+        T* DU1 = U1 + Q * N;
+        T* N1 = DU1 + Q * N;
+        for (int k = lane; k < N2; k += 32) {
+            const int a = k % N, b = k / N;
+            const int base = a * st[t1] + b * st[t2];
+            T v[N];
+#pragma unroll
+            for (int c = 0; c < N; ++c) v[c] = U[base + c * st[d]];
+            T acc = 0;
+#pragma unroll
+            for (int c = 0; c < N; ++c) acc += sDL[fn * N + c] * v[c];
+            uf[k] = fn ? v[N - 1] : v[0];
+            df[k] = acc;
+        }
+        __syncwarp();
+        const T* Im1 = sFT + L.ft.off[N - kMinN][Q - kMinN][s.p0];
+        const T* Dm1 = Im1 + Q * N;
+        for (int k = lane; k < Q * N; k += 32) {
+            const int i1 = k % Q, b = k / Q;
+            T su = 0, sd = 0, sn = 0;
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+                const T iv = Im1[i1 * N + a], dv = Dm1[i1 * N + a];
+                const T u = uf[a + N * b];
+                su += iv * u;
+                sd += dv * u;
+                sn += iv * df[a + N * b];
+            }
+            U1[k] = su;
+            DU1[k] = sd;
+            N1[k] = sn;
+        }
+        __syncwarp();
+        const T* Im2 = sFT + L.ft.off[N - kMinN][Q - kMinN][s.p1];
+        const T* Dm2 = Im2 + Q * N;
+        const T* mg = L.mg + 7 * s.goff + (s.side == 0 ? 1 : 4) * Q2;
+        T* out = mt + 4 * s.goff + 2 * s.side * Q2;
+        for (int k = lane; k < Q2; k += 32) {
+            const int i1 = k % Q, i2 = k / Q;
+            T u = 0, g1 = 0, g2 = 0, gn = 0;
+#pragma unroll
+            for (int b = 0; b < N; ++b) {
+                const T iv = Im2[i2 * N + b], dv = Dm2[i2 * N + b];
+                const T ub = U1[i1 + Q * b];
+                u += iv * ub;
+                g1 += iv * DU1[i1 + Q * b];
+                g2 += dv * ub;
+                gn += iv * N1[i1 + Q * b];
+            }
+            out[k] = u;
+            out[Q2 + k] = mg[t1 * Q2 + k] * g1 + mg[t2 * Q2 + k] * g2 + mg[d * Q2 + k] * gn;
+        }
+        __syncwarp();
+    }
+}
+
+// Flux at the mortar points and lift into Y for one mortar of the element.
+template <int N, int Q, typename T>
+__device__ __forceinline__ void lift_slot(const LevelView<T>& L, const SlotInfo<T>& s, bool interior, T sig,
+                                          T* __restrict__ Y, const T* __restrict__ sDL, const T* __restrict__ sFT,
+                                          T* F, const T* __restrict__ mt, int lane) {
+    if constexpr (Q < N) {
+        return;
+    } else {
+        constexpr int N2 = N * N, Q2 = Q * Q;
+        const int st[3] = {1, N, N2};
+        const int d = s.f >> 1, fn = (s.f & 1) ? N - 1 : 0;
+        int t1, t2;
+        tangential(d, t1, t2);
+        T* PA = F;
+        T* PB1 = PA + Q2;
+        T* PB2 = PB1 + Q2;
+        T* PBn = PB2 + Q2;
+        T* X1 = PBn + Q2;
+        T* X2 = X1 + Q * N;
+        T* X3 = X2 + Q * N;
+        const T* m = mt + 4 * s.goff;
+        const T* mg = L.mg + 7 * s.goff;
+        const T* co = mg + (s.side == 0 ? 1 : 4) * Q2;
+        const T sgn = s.side == 0 ? T(1) : T(-1);
+        for (int k = lane; k < Q2; k += 32) {
+            const T wS = mg[k];
+            const T uA = m[k], dA = m[Q2 + k];
+            T jmp, avg, bc;
+            if (interior) {
+                const T uB = m[2 * Q2 + k], dB = m[3 * Q2 + k];
+                jmp = sgn * (uA - uB);
+                avg = T(0.5) * sgn * (dA + dB);
+                bc = T(-0.5) * wS * jmp;
+            } else {
+                jmp = uA;
+                avg = dA;
+                bc = -wS * jmp;
+            }
+            const T b2 = bc * sgn;
+            PA[k] = wS * (sig * jmp - avg);
+            PB1[k] = b2 * co[t1 * Q2 + k];
+            PB2[k] = b2 * co[t2 * Q2 + k];
+            PBn[k] = b2 * co[d * Q2 + k];
+        }
+        __syncwarp();
+        const T* Im2 = sFT + L.ft.off[N - kMinN][Q - kMinN][s.p1];
+        const T* Dm2 = Im2 + Q * N;
+        for (int k = lane; k < Q * N; k += 32) {
+            const int i1 = k % Q, b = k / Q;
+            T s1v = 0, s2v = 0, s3v = 0;
+#pragma unroll
+            for (int i2 = 0; i2 < Q; ++i2) {
+                const T iv = Im2[i2 * N + b], dv = Dm2[i2 * N + b];
+                s1v += iv * PA[i1 + Q * i2] + dv * PB2[i1 + Q * i2];
+                s2v += iv * PB1[i1 + Q * i2];
+                s3v += iv * PBn[i1 + Q * i2];
+            }
+            X1[k] = s1v;
+            X2[k] = s2v;
+            X3[k] = s3v;
+        }
+        __syncwarp();
+        const T* Im1 = sFT + L.ft.off[N - kMinN][Q - kMinN][s.p0];
+        const T* Dm1 = Im1 + Q * N;
+        for (int k = lane; k < N2; k += 32) {
+            const int a = k % N, b = k / N;
+            T fu = 0, fd = 0;
+#pragma unroll
+            for (int i1 = 0; i1 < Q; ++i1) {
+                const T iv = Im1[i1 * N + a], dv = Dm1[i1 * N + a];
+                fu += iv * X1[i1 + Q * b] + dv * X2[i1 + Q * b];
+                fd += iv * X3[i1 + Q * b];
+            }
+            const int base = a * st[t1] + b * st[t2];
+            Y[base + fn * st[d]] += fu;
+#pragma unroll
+            for (int c = 0; c < N; ++c) Y[base + c * st[d]] += sDL[fn * N + c] * fd;
+        }
+        __syncwarp();
+    }
+}
+
+#define DG_Q_SWITCH(QV, CALL)                                            \
+    switch (QV) {                                                        \
+        case 2: { constexpr int Q = 2; CALL; break; }                   \
+        case 3: { constexpr int Q = 3; CALL; break; }                   \
+        case 4: { constexpr int Q = 4; CALL; break; }                   \
+        case 5: { constexpr int Q = 5; CALL; break; }                   \
+        case 6: { constexpr int Q = 6; CALL; break; }                   \
+        case 7: { constexpr int Q = 7; CALL; break; }                   \
+        case 8: { constexpr int Q = 8; CALL; break; }                   \
+        default: { constexpr int Q = 9; CALL; break; }                  \
+    }
+
 template <int N>
 struct Layout {
     static constexpr int N2 = N * N, N3 = N2 * N;
-    static constexpr int FACE = 2 * N2 + 2 * kQ * kQ + 6 * kQ * N + 3 * kQ * kQ + 4 * kQ * kQ;
-    static constexpr bool ALIAS = 4 * N3 >= FACE;   // face scratch reuses the volume scratch
-    static constexpr int WARP = ALIAS ? 6 * N3 : 6 * N3 + FACE;
+    static constexpr int TFACE = 2 * N2 + 3 * kQ * N;                 // trace kernel face scratch
+    static constexpr int TWARP = N3 + TFACE;
+    static constexpr int EFACE = 4 * kQ * kQ + 3 * kQ * N;            // element kernel face scratch
+    static constexpr bool ALIAS = 4 * N3 >= EFACE;                    // reuses the volume scratch
+    static constexpr int EWARP = ALIAS ? 6 * N3 : 6 * N3 + EFACE;
 };
 
+// Shared-memory preamble common to both kernels: mortar tables (FP32) and the
+// element's 1-D volume tables.
 template <int N, typename T>
-__global__ void apply_kernel(LevelView<T> L, const int* __restrict__ bucket, int count, const T* __restrict__ x,
-                             T* __restrict__ y) {
-    using Ly = Layout<N>;
-    constexpr int N2 = Ly::N2, N3 = Ly::N3;
-    // FP32: every mortar table is staged in shared memory (26.6 KB); FP64 reads
-    // them through L1 so that the larger FP64 scratch leaves room for more warps.
+__device__ __forceinline__ T* load_tables(const LevelView<T>& L, const T*& sFT, T*& sI, T*& sDg, T*& sDL) {
     constexpr bool STAGE = sizeof(T) == 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     const int ftot = STAGE ? L.ft.total : 0;
     T* sFTs = sm;
-    const T* sFT = STAGE ? sFTs : L.ftab;
-    T* sI = sFTs + ((ftot + 3) & ~3);
-    T* sDg = sI + N2;
-    T* sDL = sDg + N2;
-    const int nwarps = blockDim.x >> 5;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    sFT = STAGE ? sFTs : L.ftab;
+    sI = sFTs + ((ftot + 3) & ~3);
+    sDg = sI + N * N;
+    sDL = sDg + N * N;
     for (int k = threadIdx.x; k < ftot; k += blockDim.x) sFTs[k] = L.ftab[k];
-    for (int k = threadIdx.x; k < N2; k += blockDim.x) {
+    for (int k = threadIdx.x; k < N * N; k += blockDim.x) {
         sI[k] = L.tab[tab_n(TabIndex::I, N) + k];
         sDg[k] = L.tab[tab_n(TabIndex::Dg, N) + k];
         sDL[k] = L.tab[tab_n(TabIndex::DL, N) + k];
     }
     __syncthreads();
-    T* U = sDL + N2 + warp * Ly::WARP;
+    return sDL + N * N;
+}
+
+template <int N, typename T>
+__global__ void trace_kernel(LevelView<T> L, const int* __restrict__ bucket, int count, const T* __restrict__ x,
+                             T* __restrict__ mt) {
+    using Ly = Layout<N>;
+    constexpr int N3 = Ly::N3;
+    const T* sFT;
+    T *sI, *sDg, *sDL;
+    T* wbase = load_tables<N, T>(L, sFT, sI, sDg, sDL);
+    const int nwarps = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T* U = wbase + warp * Ly::TWARP;
+    T* F = U + N3;
+    for (int ei = blockIdx.x * nwarps + warp; ei < count; ei += gridDim.x * nwarps) {
+        const int e = bucket[ei];
+        const long long dofo = L.dof_off[e];
+        for (int k = lane; k < N3; k += 32) U[k] = x[dofo + k];
+        __syncwarp();
+        const int s0 = L.slot_off[e], s1 = L.slot_off[e + 1];
+        for (int si = s0; si < s1; ++si) {
+            const SlotInfo<T> s = slot_info(L, si);
+            DG_Q_SWITCH(s.q, (trace_slot<N, Q, T>(L, s, U, sDL, sFT, F, mt, lane)))
+        }
+    }
+}
+
+template <int N, typename T>
+__global__ void element_kernel(LevelView<T> L, const int* __restrict__ bucket, int count, const T* __restrict__ x,
+                               T* __restrict__ y) {
+    using Ly = Layout<N>;
+    constexpr int N2 = Ly::N2, N3 = Ly::N3;
+    const T* sFT;
+    T *sI, *sDg, *sDL;
+    T* wbase = load_tables<N, T>(L, sFT, sI, sDg, sDL);
+    const int nwarps = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T* U = wbase + warp * Ly::EWARP;
     T* Y = U + N3;
     T* A = Y + N3;
     T* B = A + N3;
@@ -108,32 +323,13 @@ __global__ void apply_kernel(LevelView<T> L, const int* __restrict__ bucket, int
     T* G3 = G1 + N3;
     T* G2 = Y;  // the y-gradient lives in Y until the backward passes
     T* F = Ly::ALIAS ? A : G3 + N3;
-    T* uf = F;
-    T* df = uf + N2;
-    T* ufn = df + N2;
-    T* dfn = ufn + kQ * kQ;
-    T* U1o = dfn + kQ * kQ;
-    T* DU1o = U1o + kQ * N;
-    T* N1o = DU1o + kQ * N;
-    T* X1 = N1o + kQ * N;
-    T* X2 = X1 + kQ * N;
-    T* X3 = X2 + kQ * N;
-    T* U1n = X3 + kQ * N;
-    T* DU1n = U1n + kQ * kQ;
-    T* N1n = DU1n + kQ * kQ;
-    T* PA = N1n + kQ * kQ;
-    T* PB1 = PA + kQ * kQ;
-    T* PB2 = PB1 + kQ * kQ;
-    T* PBn = PB2 + kQ * kQ;
     const bool mass = L.c0 != nullptr;
-    const int st[3] = {1, N, N2};
-
+    (void)N2;
     for (int ei = blockIdx.x * nwarps + warp; ei < count; ei += gridDim.x * nwarps) {
         const int e = bucket[ei];
         const long long dofo = L.dof_off[e], vo = L.vqp_off[e];
         for (int k = lane; k < N3; k += 32) U[k] = x[dofo + k];
         __syncwarp();
-        // ---- volume ----------------------------------------------------------------
         wpass<N, 0, false, false>(U, A, sI, lane);
         __syncwarp();
         wpass<N, 1, false, false>(A, B, sI, lane);
@@ -181,186 +377,13 @@ __global__ void apply_kernel(LevelView<T> L, const int* __restrict__ bucket, int
             }
             __syncwarp();
         }
-        // ---- faces ----------------------------------------------------------------------
         const int s0 = L.slot_off[e], s1 = L.slot_off[e + 1];
-        int mi_next = L.slot_mortar[s0];
-        Mortar M_next = L.mortars[mi_next];
         for (int si = s0; si < s1; ++si) {
-            const int mi = mi_next;
-            const Mortar M = M_next;
-            if (si + 1 < s1) {   // prefetch the next slot's mortar record
-                mi_next = L.slot_mortar[si + 1];
-                M_next = L.mortars[mi_next];
-            }
-            const int f = L.slot_face[si];
-            const int side = L.slot_side[si];
-            const int q = M.q, q2 = q * q;
-            const float qinv = 1.0f / (float)q;
+            const int mi = L.slot_mortar[si];
+            const SlotInfo<T> s = slot_info(L, si);
+            const bool interior = L.mortars[mi].eB >= 0;
             const T sig = L.sigma[mi];
-            int p0, p1, eo, fo, o0, o1;
-            if (side == 0) { p0 = M.posA0; p1 = M.posA1; eo = M.eB; fo = M.fB; o0 = M.posB0; o1 = M.posB1; }
-            else { p0 = M.posB0; p1 = M.posB1; eo = M.eA; fo = M.fA; o0 = M.posA0; o1 = M.posA1; }
-            const int nbN = eo >= 0 ? L.p[eo] + 1 : 2;
-            const float nbinv = 1.0f / (float)nbN;
-            const int d = f >> 1, fn = (f & 1) ? N - 1 : 0;
-            int t1, t2;
-            tangential(d, t1, t2);
-            // S1: own trace u and d_nu u at own face nodes; the neighbour's from x
-            for (int k = lane; k < N2; k += 32) {
-                const int a = k % N, b = k / N;
-                const int base = a * st[t1] + b * st[t2];
-                uf[k] = U[base + fn * st[d]];
-                T acc = 0;
-#pragma unroll
-                for (int c = 0; c < N; ++c) acc += sDL[fn * N + c] * U[base + c * st[d]];
-                df[k] = acc;
-            }
-            if (eo >= 0) {
-                const T* xe = x + L.dof_off[eo];
-                const int nst[3] = {1, nbN, nbN * nbN};
-                const int fno = (fo & 1) ? nbN - 1 : 0;
-                const T* DLn = L.tab + tab_n(TabIndex::DL, nbN) + fno * nbN;
-                for (int k = lane; k < nbN * nbN; k += 32) {
-                    int a, b;
-                    split(k, nbN, nbinv, a, b);
-                    const int base = a * nst[t1] + b * nst[t2];
-                    T acc = 0, fv = 0;
-                    for (int c = 0; c < nbN; ++c) {
-                        const T v = __ldg(xe + base + c * nst[d]);
-                        acc += DLn[c] * v;
-                        if (c == fno) fv = v;
-                    }
-                    ufn[k] = fv;
-                    dfn[k] = acc;
-                }
-            }
-            __syncwarp();
-            const T* Im1 = sFT + L.ft.off[N - kMinN][q - kMinN][p0];
-            const T* Dm1 = Im1 + q * N;
-            const T* Im2 = sFT + L.ft.off[N - kMinN][q - kMinN][p1];
-            const T* Dm2 = Im2 + q * N;
-            // S2: interpolate along the first tangential axis
-            for (int k = lane; k < q * N; k += 32) {
-                int i1, b;
-                split(k, q, qinv, i1, b);
-                T su = 0, sd = 0, sn = 0;
-#pragma unroll
-                for (int a = 0; a < N; ++a) {
-                    const T iv = Im1[i1 * N + a], dv = Dm1[i1 * N + a];
-                    const T u = uf[a + N * b];
-                    su += iv * u;
-                    sd += dv * u;
-                    sn += iv * df[a + N * b];
-                }
-                U1o[k] = su;
-                DU1o[k] = sd;
-                N1o[k] = sn;
-            }
-            const T* Im1n = nullptr;
-            const T* Im2n = nullptr;
-            if (eo >= 0) {
-                Im1n = sFT + L.ft.off[nbN - kMinN][q - kMinN][o0];
-                Im2n = sFT + L.ft.off[nbN - kMinN][q - kMinN][o1];
-                const T* Dm1n = Im1n + q * nbN;
-                for (int k = lane; k < q * nbN; k += 32) {
-                    int i1, b;
-                split(k, q, qinv, i1, b);
-                    T su = 0, sd = 0, sn = 0;
-                    for (int a = 0; a < nbN; ++a) {
-                        const T iv = Im1n[i1 * nbN + a], dv = Dm1n[i1 * nbN + a];
-                        const T u = ufn[a + nbN * b];
-                        su += iv * u;
-                        sd += dv * u;
-                        sn += iv * dfn[a + nbN * b];
-                    }
-                    U1n[k] = su;
-                    DU1n[k] = sd;
-                    N1n[k] = sn;
-                }
-            }
-            __syncwarp();
-            // S3: values at the mortar points, numerical flux, lift coefficients
-            {
-                const T* mg = L.mg + 7 * M.goff;
-                const T sgn = side == 0 ? T(1) : T(-1);
-                const int oo = side == 0 ? 1 : 4, on = side == 0 ? 4 : 1;
-                for (int k = lane; k < q2; k += 32) {
-                    int i1, i2;
-                split(k, q, qinv, i1, i2);
-                    T u = 0, gt1 = 0, gt2 = 0, gn = 0;
-#pragma unroll
-                    for (int b = 0; b < N; ++b) {
-                        const T iv = Im2[i2 * N + b], dv = Dm2[i2 * N + b];
-                        const T ub = U1o[i1 + q * b];
-                        u += iv * ub;
-                        gt1 += iv * DU1o[i1 + q * b];
-                        gt2 += dv * ub;
-                        gn += iv * N1o[i1 + q * b];
-                    }
-                    const T wS = mg[k];
-                    const T co1 = sgn * mg[(oo + t1) * q2 + k], co2 = sgn * mg[(oo + t2) * q2 + k];
-                    const T cod = sgn * mg[(oo + d) * q2 + k];
-                    const T dno = co1 * gt1 + co2 * gt2 + cod * gn;
-                    T jmp, avg, bc;
-                    if (eo >= 0) {
-                        const T* Dm2n = Im2n + q * nbN;
-                        T un = 0, ht1 = 0, ht2 = 0, hn = 0;
-                        for (int b = 0; b < nbN; ++b) {
-                            const T iv = Im2n[i2 * nbN + b], dv = Dm2n[i2 * nbN + b];
-                            const T ub = U1n[i1 + q * b];
-                            un += iv * ub;
-                            ht1 += iv * DU1n[i1 + q * b];
-                            ht2 += dv * ub;
-                            hn += iv * N1n[i1 + q * b];
-                        }
-                        const T dnn = sgn * (mg[(on + t1) * q2 + k] * ht1 + mg[(on + t2) * q2 + k] * ht2 +
-                                             mg[(on + d) * q2 + k] * hn);
-                        jmp = u - un;
-                        avg = T(0.5) * (dno + dnn);
-                        bc = T(-0.5) * wS * jmp;
-                    } else {
-                        jmp = u;
-                        avg = dno;
-                        bc = -wS * jmp;
-                    }
-                    PA[k] = wS * (sig * jmp - avg);
-                    PB1[k] = bc * co1;
-                    PB2[k] = bc * co2;
-                    PBn[k] = bc * cod;
-                }
-            }
-            __syncwarp();
-            // S4: transposed interpolation along the second tangential axis
-            for (int k = lane; k < q * N; k += 32) {
-                int i1, b;
-                split(k, q, qinv, i1, b);
-                T s1v = 0, s2v = 0, s3v = 0;
-                for (int i2 = 0; i2 < q; ++i2) {
-                    const T iv = Im2[i2 * N + b], dv = Dm2[i2 * N + b];
-                    s1v += iv * PA[i1 + q * i2] + dv * PB2[i1 + q * i2];
-                    s2v += iv * PB1[i1 + q * i2];
-                    s3v += iv * PBn[i1 + q * i2];
-                }
-                X1[k] = s1v;
-                X2[k] = s2v;
-                X3[k] = s3v;
-            }
-            __syncwarp();
-            // S5: transposed interpolation along the first axis and lift into y
-            for (int k = lane; k < N2; k += 32) {
-                const int a = k % N, b = k / N;
-                T fu = 0, fd = 0;
-                for (int i1 = 0; i1 < q; ++i1) {
-                    const T iv = Im1[i1 * N + a], dv = Dm1[i1 * N + a];
-                    fu += iv * X1[i1 + q * b] + dv * X2[i1 + q * b];
-                    fd += iv * X3[i1 + q * b];
-                }
-                const int base = a * st[t1] + b * st[t2];
-                Y[base + fn * st[d]] += fu;
-#pragma unroll
-                for (int c = 0; c < N; ++c) Y[base + c * st[d]] += sDL[fn * N + c] * fd;
-            }
-            __syncwarp();
+            DG_Q_SWITCH(s.q, (lift_slot<N, Q, T>(L, s, interior, sig, Y, sDL, sFT, F, L.mt, lane)))
         }
         for (int k = lane; k < N3; k += 32) y[dofo + k] = Y[k];
         __syncwarp();
@@ -372,63 +395,105 @@ inline int& sm_count() {
     return v;
 }
 
-template <int N, typename T>
-cudaError_t launch_n(const LevelView<T>& L, const BucketInfo& b, const T* x, T* y, cudaStream_t st) {
-    using Ly = Layout<N>;
-    static int W = 0;
-    static size_t smem = 0;
-    if (W == 0) {
-        // one persistent CTA per SM; warps limited by shared memory (tables staged once per CTA)
-        // and by the register file
-        const size_t table_vals = (sizeof(T) == 4 ? ((L.ft.total + 3) & ~3) : 0) + 3 * N * N;
-        const size_t cap = 220 * 1024;
-        cudaError_t err = cudaFuncSetAttribute(apply_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)cap);
+// Warps per CTA and resident CTAs per SM: the configuration with the most
+// resident warps (up to 32 per CTA) that shared memory and registers allow.
+template <typename K>
+cudaError_t pick_warps(K kernel, size_t table_bytes, size_t warp_bytes, int& W, size_t& smem, int& per_sm) {
+    const size_t cap = 220 * 1024;
+    cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+    if (err != cudaSuccess) return err;
+    int best_w = 1, best_blocks = 1, best_res = 0;
+    for (int w = 1; w <= 32; ++w) {
+        const size_t bytes = table_bytes + (size_t)w * warp_bytes;
+        if (bytes > cap) break;
+        int blocks = 0;
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, w * 32, bytes);
         if (err != cudaSuccess) return err;
-        int w = (int)((cap - table_vals * sizeof(T)) / (Ly::WARP * sizeof(T)));
-        if (w > 24) w = 24;
-        for (; w > 1; --w) {   // largest warp count of which one CTA fits on an SM
-            const size_t sm_bytes = (table_vals + (size_t)w * Ly::WARP) * sizeof(T);
-            int blocks = 0;
-            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, apply_kernel<N, T>, w * 32, sm_bytes);
-            if (err != cudaSuccess) return err;
-            if (blocks >= 1) break;
+        if (blocks >= 1 && blocks * w >= best_res) {   // ties -> larger CTAs (fewer table copies)
+            best_res = blocks * w;
+            best_w = w;
+            best_blocks = blocks;
         }
-        W = w;
-        smem = (table_vals + (size_t)W * Ly::WARP) * sizeof(T);
     }
-    int& g_sm_count = sm_count();
-    if (g_sm_count == 0) {
+    W = best_w;
+    per_sm = best_blocks;
+    smem = table_bytes + (size_t)W * warp_bytes;
+    return cudaSuccess;
+}
+
+inline int grid_cap() {
+    int& g = sm_count();
+    if (g == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
-        if (g_sm_count <= 0) g_sm_count = 152;
+        cudaDeviceGetAttribute(&g, cudaDevAttrMultiProcessorCount, dev);
+        if (g <= 0) g = 152;
+    }
+    return g;
+}
+
+template <int N, typename T>
+cudaError_t launch_trace(const LevelView<T>& L, const BucketInfo& b, const T* x, cudaStream_t st) {
+    using Ly = Layout<N>;
+    static int W = 0, per_sm = 1;
+    static size_t smem = 0;
+    if (W == 0) {
+        const size_t table_bytes = ((sizeof(T) == 4 ? ((L.ft.total + 3) & ~3) : 0) + 3 * N * N) * sizeof(T);
+        cudaError_t err = pick_warps(trace_kernel<N, T>, table_bytes, Ly::TWARP * sizeof(T), W, smem, per_sm);
+        if (err != cudaSuccess) return err;
     }
     int grid = (b.count + W - 1) / W;
-    if (grid > g_sm_count) grid = g_sm_count;
-    apply_kernel<N, T><<<grid, W * 32, smem, st>>>(L, b.elems, b.count, x, y);
+    if (grid > grid_cap() * per_sm) grid = grid_cap() * per_sm;
+    trace_kernel<N, T><<<grid, W * 32, smem, st>>>(L, b.elems, b.count, x, L.mt);
     return cudaGetLastError();
 }
+
+template <int N, typename T>
+cudaError_t launch_element(const LevelView<T>& L, const BucketInfo& b, const T* x, T* y, cudaStream_t st) {
+    using Ly = Layout<N>;
+    static int W = 0, per_sm = 1;
+    static size_t smem = 0;
+    if (W == 0) {
+        const size_t table_bytes = ((sizeof(T) == 4 ? ((L.ft.total + 3) & ~3) : 0) + 3 * N * N) * sizeof(T);
+        cudaError_t err = pick_warps(element_kernel<N, T>, table_bytes, Ly::EWARP * sizeof(T), W, smem, per_sm);
+        if (err != cudaSuccess) return err;
+    }
+    int grid = (b.count + W - 1) / W;
+    if (grid > grid_cap() * per_sm) grid = grid_cap() * per_sm;
+    element_kernel<N, T><<<grid, W * 32, smem, st>>>(L, b.elems, b.count, x, y);
+    return cudaGetLastError();
+}
+
+#define DG_N_SWITCH(NV, CALL)                              \
+    switch (NV) {                                          \
+        case 2: { constexpr int NN = 2; CALL; break; }     \
+        case 3: { constexpr int NN = 3; CALL; break; }     \
+        case 4: { constexpr int NN = 4; CALL; break; }     \
+        case 5: { constexpr int NN = 5; CALL; break; }     \
+        case 6: { constexpr int NN = 6; CALL; break; }     \
+        case 7: { constexpr int NN = 7; CALL; break; }     \
+        case 8: { constexpr int NN = 8; CALL; break; }     \
+        default: { constexpr int NN = 9; CALL; break; }    \
+    }
 
 }  // namespace apply_detail
 
 template <typename T>
 cudaError_t launch_apply(const LevelView<T>& L, const BucketInfo* buckets, const T* x, T* y, cudaStream_t st,
                          int* launches) {
-    for (int n = kMinN; n <= kMaxN; ++n) {
+    for (int n = kMinN; n <= kMaxN; ++n) {   // every element's mortar traces first ...
         const BucketInfo& b = buckets[n];
         if (b.count == 0) continue;
         cudaError_t err = cudaSuccess;
-        switch (n) {
-            case 2: err = apply_detail::launch_n<2, T>(L, b, x, y, st); break;
-            case 3: err = apply_detail::launch_n<3, T>(L, b, x, y, st); break;
-            case 4: err = apply_detail::launch_n<4, T>(L, b, x, y, st); break;
-            case 5: err = apply_detail::launch_n<5, T>(L, b, x, y, st); break;
-            case 6: err = apply_detail::launch_n<6, T>(L, b, x, y, st); break;
-            case 7: err = apply_detail::launch_n<7, T>(L, b, x, y, st); break;
-            case 8: err = apply_detail::launch_n<8, T>(L, b, x, y, st); break;
-            case 9: err = apply_detail::launch_n<9, T>(L, b, x, y, st); break;
-        }
+        DG_N_SWITCH(n, (err = apply_detail::launch_trace<NN, T>(L, b, x, st)))
+        if (err != cudaSuccess) return err;
+        if (launches) ++*launches;
+    }
+    for (int n = kMinN; n <= kMaxN; ++n) {   // ... then volume + face lifts
+        const BucketInfo& b = buckets[n];
+        if (b.count == 0) continue;
+        cudaError_t err = cudaSuccess;
+        DG_N_SWITCH(n, (err = apply_detail::launch_element<NN, T>(L, b, x, y, st)))
         if (err != cudaSuccess) return err;
         if (launches) ++*launches;
     }

@@ -64,6 +64,7 @@ LevelView<double> view<double>(dg_ctx* c, int l) {
     v.ft = c->ft;
     v.ob_total = (long long)L.ob_count;
     v.chk = device_check_flag();
+    v.mt = L.mt64;
     return v;
 }
 
@@ -91,6 +92,7 @@ LevelView<float> view<float>(dg_ctx* c, int l) {
     v.ft = c->ft;
     v.ob_total = (long long)L.ob_count;
     v.chk = device_check_flag();
+    v.mt = L.mt32;
     return v;
 }
 
@@ -297,6 +299,58 @@ int vcycle_t(dg_ctx* c, const T* f, T* v, const dg_mg_opts* o) {
     return DG_OK;
 }
 
+bool same_opts(const dg_mg_opts& a, const dg_mg_opts* b) {
+    const dg_mg_opts z{};
+    const dg_mg_opts& bb = b ? *b : z;
+    return a.coarse == bb.coarse && a.cheb.n_eigs == bb.cheb.n_eigs && a.cheb.n_cheb == bb.cheb.n_cheb &&
+           a.cheb.Lambda == bb.cheb.Lambda;
+}
+
+// The V-cycle of one FCG iteration (FP64: r -> v; FP32: fcg32[0] -> fcg32[1]).
+// graph_mode 0 on a non-default stream: the first call for a given precision /
+// options / argument epoch runs eagerly (allocations, attributes) and then
+// captures the same launch sequence into a CUDA graph; later calls replay it.
+int vcycle_maybe_graph(dg_ctx* c, int prec, double* r, double* v, const dg_mg_opts* mo, int graph_mode) {
+    auto eager = [&]() -> int {
+        if (prec == DG_FP32) return vcycle_t<float>(c, c->fcg32[0], c->fcg32[1], mo);
+        return vcycle_t<double>(c, r, v, mo);
+    };
+    if (graph_mode != 0 || c->st == nullptr) return eager();
+    if (c->vgraph && c->vgraph_prec == prec && c->vgraph_epoch == c->epoch && same_opts(c->vgraph_opts, mo)) {
+        CK(cudaGraphLaunch(c->vgraph, c->st));
+        c->launches += c->vgraph_launches;
+        return DG_OK;
+    }
+    int rc = eager();
+    if (rc) return rc;
+    if (c->vgraph) {
+        cudaGraphExecDestroy(c->vgraph);
+        c->vgraph = nullptr;
+    }
+    const long long before = c->launches;
+    CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+    rc = eager();
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->st, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(DG_ERR_CUDA, std::string("V-cycle graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->vgraph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->vgraph = nullptr;
+        return fail(DG_ERR_CUDA, std::string("V-cycle graph instantiate: ") + cudaGetErrorString(e));
+    }
+    c->vgraph_launches = c->launches - before;
+    c->launches = before;   // captured, not executed
+    c->vgraph_prec = prec;
+    c->vgraph_epoch = c->epoch;
+    c->vgraph_opts = mo ? *mo : dg_mg_opts{};
+    return DG_OK;
+}
+
 int upload_level(dg_ctx* c, LevelDev& L, int li, std::string& err) {
     Arena& A = c->arena;
     cudaStream_t st = c->st;
@@ -341,6 +395,8 @@ int upload_level(dg_ctx* c, LevelDev& L, int li, std::string& err) {
     L.bxyz = A.alloc<double>(3 * nb);
     L.G32 = A.alloc<float>(6 * nv);
     L.mg32 = A.alloc<float>(7 * nm);
+    L.mt64 = A.alloc<double>(4 * nm);
+    L.mt32 = A.alloc<float>(4 * nm);
     L.sigma32 = A.alloc<float>(nmort);
     int* bad = A.alloc<int>(1);
     double* X = nullptr;
@@ -419,6 +475,7 @@ size_t level_bytes(const LevelHost& h) {
     size_t b = 0;
     b += nv * (6 * 8 + 8 + 24 + 6 * 4);        // G64, wdetJ, vxyz, G32
     b += nm * 7 * (8 + 4);                     // mortar geometry
+    b += nm * 4 * (8 + 4);                     // mortar trace buffers
     b += h.mortars.size() * (sizeof(Mortar) + 12);
     b += h.slot_mortar.size() * 6 + h.n_elems() * 40;
     b += nd * 6 * (8 + 4);                     // solver work vectors, both precisions
@@ -501,6 +558,7 @@ void dg_ctx_destroy(dg_ctx* c) {
     if (!c) return;
     if (c->st) cudaStreamSynchronize(c->st);
     else cudaDeviceSynchronize();
+    if (c->vgraph) cudaGraphExecDestroy(c->vgraph);
     c->arena.free_all();
     if (c->red_host) cudaFreeHost(c->red_host);
     delete c;
@@ -521,6 +579,16 @@ int dg_level_info_get(dg_ctx* c, int level, dg_level_info* info) {
     for (int v : h.p) mp = std::max(mp, v);
     info->max_p = mp;
     info->device_bytes = c->arena.bytes;
+    double fl = 0.0;
+    for (int e = 0; e < h.n_elems(); ++e) {
+        const double n = h.p[e] + 1;
+        fl += 24.0 * n * n * n * n + 18.0 * n * n * n;
+        for (int si = h.slot_off[e]; si < h.slot_off[e + 1]; ++si) {
+            const double q = h.mortars[h.slot_mortar[si]].q;
+            fl += 4.0 * n * n * n + 12.0 * q * n * n + 16.0 * q * q * n + 20.0 * q * q;
+        }
+    }
+    info->apply_flops = fl;
     return DG_OK;
 }
 
@@ -656,13 +724,16 @@ int dg_solve(dg_ctx* c, const double* b, double* x, const dg_solver_opts* o, dg_
         // v = VCYCLE(r)
         if (!use_mg) {
             CK(cudaMemcpyAsync(v, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-        } else if (mgp == DG_FP32) {
-            CK(cast_d2f(r, c->fcg32[0], n, st));
-            if ((rc = vcycle_t<float>(c, c->fcg32[0], c->fcg32[1], mo))) return rc;
-            CK(cast_f2d(c->fcg32[1], v, n, st));
-            c->launches += 2;
         } else {
-            if ((rc = vcycle_t<double>(c, r, v, mo))) return rc;
+            if (mgp == DG_FP32) {
+                CK(cast_d2f(r, c->fcg32[0], n, st));
+                c->launches += 1;
+            }
+            if ((rc = vcycle_maybe_graph(c, mgp, r, v, mo, o ? o->graph_mode : 0))) return rc;
+            if (mgp == DG_FP32) {
+                CK(cast_f2d(c->fcg32[1], v, n, st));
+                c->launches += 1;
+            }
         }
         if ((rc = apply_t<double>(c, Lt, v, w))) return rc;
         {

@@ -55,6 +55,8 @@ struct LevelDev {
     BucketInfo buckets[kMaxN + 1] = {};
     double *G64 = nullptr, *wdetJ = nullptr, *vxyz = nullptr, *mg64 = nullptr, *sigma64 = nullptr, *bxyz = nullptr;
     float *G32 = nullptr, *mg32 = nullptr, *sigma32 = nullptr;
+    double* mt64 = nullptr;           // mortar trace buffers of the apply
+    float* mt32 = nullptr;
     double* c0_64 = nullptr;
     float* c0_32 = nullptr;
     double* Ob64 = nullptr;
@@ -99,5 +101,12 @@ struct dg_ctx {
     double* p_beta = nullptr;
     double* nw[4] = {};             // Newton work vectors (double, finest): R, du, Lu, S
     bool galerkin_ready = false;
+    // CUDA graph of the V-cycle used inside dg_solve (captured once, replayed)
+    cudaGraphExec_t vgraph = nullptr;
+    int vgraph_prec = -1;
+    long long vgraph_epoch = -1;
+    long long vgraph_launches = 0;  // kernels in the graph
+    dg_mg_opts vgraph_opts{};
+    long long epoch = 0;            // bumped whenever kernel arguments of the solver change
     long long launches = 0;
 };

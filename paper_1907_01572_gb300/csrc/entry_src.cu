@@ -108,14 +108,20 @@ int build_galerkin(dg_ctx* c) {
         g.chk = device_check_flag();
         CK2(launch_galerkin(g, F.c0_64, L.Ob64, L.Ob32, c->st));
         c->launches += 1;
+        if (!L.z_active) ++c->epoch;
         L.z_active = true;
     }
+    if (!F.z_active) ++c->epoch;
     F.z_active = true;
     return DG_OK;
 }
 
 void set_zeroth_active(dg_ctx* c, bool on) {
-    for (auto& L : c->lv) L.z_active = on && (L.c0_64 != nullptr || L.Ob64 != nullptr);
+    for (auto& L : c->lv) {
+        const bool v = on && (L.c0_64 != nullptr || L.Ob64 != nullptr);
+        if (v != L.z_active) ++c->epoch;   // kernel arguments of the captured V-cycle change
+        L.z_active = v;
+    }
 }
 
 int ensure_newton_work(dg_ctx* c) {

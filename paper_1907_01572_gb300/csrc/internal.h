@@ -123,6 +123,7 @@ struct LevelView {         // passed by value to kernels
     FaceTabs ft;
     long long ob_total;    // entries of Ob (bounds check)
     int* chk;              // self-check flag
+    T* mt;                 // mortar trace buffer: 4 * n_mortar_pts ([u_A, dn_A, u_B, dn_B] per mortar)
 };
 
 // Self-check support: kernels that index with offsets read from tables check

@@ -78,6 +78,7 @@ LevelView<T> static_view(dg_ctx* c, int l) {
         v.sigma = (const T*)L.sigma64;
         v.tab = (const T*)c->tab64;
         v.ftab = (const T*)c->ftab64;
+        v.mt = (T*)L.mt64;
     } else {
         v.G = (const T*)L.G32;
         v.c0 = L.z_active ? (const T*)L.c0_32 : nullptr;
@@ -86,6 +87,7 @@ LevelView<T> static_view(dg_ctx* c, int l) {
         v.sigma = (const T*)L.sigma32;
         v.tab = (const T*)c->tab32;
         v.ftab = (const T*)c->ftab32;
+        v.mt = (T*)L.mt32;
     }
     v.ft = c->ft;
     v.ob_total = (long long)L.ob_count;

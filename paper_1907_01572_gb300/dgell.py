@@ -37,7 +37,7 @@ class dg_disc_opts(ctypes.Structure):
 class dg_level_info(ctypes.Structure):
     _fields_ = [("n_levels", ctypes.c_int), ("n_elems", ctypes.c_int), ("n_dofs", ctypes.c_int64),
                 ("n_vol_qp", ctypes.c_int64), ("n_bnd_qp", ctypes.c_int64), ("n_mortars", ctypes.c_int),
-                ("max_p", ctypes.c_int), ("device_bytes", ctypes.c_size_t)]
+                ("max_p", ctypes.c_int), ("device_bytes", ctypes.c_size_t), ("apply_flops", ctypes.c_double)]
 
 
 class dg_cheb_opts(ctypes.Structure):
@@ -50,7 +50,7 @@ class dg_mg_opts(ctypes.Structure):
 
 class dg_solver_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mg_prec", ctypes.c_int),
-                ("use_mg", ctypes.c_int), ("mg", dg_mg_opts)]
+                ("use_mg", ctypes.c_int), ("mg", dg_mg_opts), ("graph_mode", ctypes.c_int)]
 
 
 class dg_solve_stats(ctypes.Structure):
@@ -173,8 +173,8 @@ def mg_opts(n_eigs=15, n_cheb=15, Lambda=20.0, coarse=0):
     return dg_mg_opts(cheb_opts(n_eigs, n_cheb, Lambda), coarse)
 
 
-def solver_opts(tol=1e-10, max_iter=100, mg_prec=DG_FP64, use_mg=1, **mg):
-    return dg_solver_opts(tol, max_iter, mg_prec, use_mg, mg_opts(**mg))
+def solver_opts(tol=1e-10, max_iter=100, mg_prec=DG_FP64, use_mg=1, graph_mode=0, **mg):
+    return dg_solver_opts(tol, max_iter, mg_prec, use_mg, mg_opts(**mg), graph_mode)
 
 
 class Context:

@@ -125,3 +125,117 @@ def random_vector(n, seed=1):
 def oracle_mesh_args(desc):
     """Positional/keyword arguments for the oracle's Mesh constructor."""
     return (desc['lo'], desc['hi'], desc['leaves'], desc['p']), dict(warp=desc['warp'])
+
+
+# ---- radially symmetric star with a density jump (-Lap u = 4 pi rho) -------------
+def star_density(r):
+    """rho(r) = (1 - r^2) for 0.5 <= r < 1, 0.6 (1 - r^2) for r < 0.5, 0 outside."""
+    r = np.asarray(r, dtype=np.float64)
+    rho = np.where(r < 1.0, 1.0 - r * r, 0.0)
+    return np.where(r < 0.5, 0.6 * rho, rho)
+
+
+def star_solution(x):
+    """Exact u of -Lap u = 4 pi rho with u -> 0 at infinity:
+    u(r) = M(r)/r + int_r^inf 4 pi rho(s) s ds,  M(r) = int_0^r 4 pi rho(s) s^2 ds."""
+    x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
+    r = np.linalg.norm(x, axis=1)
+    P = lambda s: s ** 3 / 3.0 - s ** 5 / 5.0          # int s^2 (1 - s^2)
+    Q = lambda s: s ** 2 / 2.0 - s ** 4 / 4.0          # int s (1 - s^2)
+    h = 0.5
+    M_in = 4 * np.pi * 0.6 * P(np.minimum(r, h))
+    M_mid = 4 * np.pi * (P(np.clip(r, h, 1.0)) - P(h))
+    M = M_in + np.where(r > h, M_mid, 0.0)
+    K_mid = 4 * np.pi * (Q(1.0) - Q(np.clip(r, h, 1.0)))
+    K_in = 4 * np.pi * 0.6 * (Q(h) - Q(np.minimum(r, h)))
+    K = np.where(r < 1.0, K_mid, 0.0) + np.where(r < h, K_in, 0.0)
+    rs = np.maximum(r, 1e-300)
+    return np.where(r > 0, M / rs, 0.0) + K
+
+
+def star_source(x):
+    x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
+    return 4 * np.pi * star_density(np.linalg.norm(x, axis=1))
+
+
+def _cell_bounds(lf, lo, hi):
+    L, i, j, k = lf
+    w = (np.asarray(hi) - np.asarray(lo)) / (1 << L)
+    a = np.asarray(lo) + w * np.array([i, j, k])
+    return a, a + w
+
+
+def _dist_range(a, b, c=(0.0, 0.0, 0.0)):
+    c = np.asarray(c, dtype=np.float64)
+    near = np.clip(c, a, b)
+    dmin = np.linalg.norm(near - c)
+    far = np.where(np.abs(a - c) > np.abs(b - c), a, b)
+    return dmin, np.linalg.norm(far - c)
+
+
+def star_mesh(R=4.0, level=3, refine=2, seed=3, p_cut=4, p_lo=5, p_hi=8):
+    """Box [-R, R]^3, uniform level `level`, cells cut by the spheres r = 0.5 and
+    r = 1 refined `refine` times (2:1 balanced); p = p_cut on the finest cut
+    cells, p ~ U{p_lo..p_hi} (seed) elsewhere."""
+    lo, hi = (-R, -R, -R), (R, R, R)
+    leaves = uniform_leaves(level)
+
+    def cut(lf):
+        a, b = _cell_bounds(lf, lo, hi)
+        dmin, dmax = _dist_range(a, b)
+        return any(dmin <= s <= dmax for s in (0.5, 1.0))
+
+    for _ in range(refine):
+        leaves = refine_(leaves, cut)
+        leaves = balance_2to1(leaves)
+    leaves = morton_sort(leaves)
+    rng = np.random.default_rng(seed)
+    maxL = max(lf[0] for lf in leaves)
+    p = rng.integers(p_lo, p_hi + 1, size=len(leaves))
+    p = np.array([p_cut if (lf[0] == maxL and cut(lf)) else pv for lf, pv in zip(leaves, p)], dtype=np.int32)
+    return dict(lo=lo, hi=hi, leaves=np.array(leaves, dtype=np.int32), p=p, warp=None)
+
+
+refine_ = refine
+
+
+# ---- puncture initial data -----------------------------------------------------------
+def two_punctures():
+    """m = 0.5 at (+-3, 0, 0) with momenta +-0.2 along y (zero spin); the
+    positions are shifted off the element faces of the meshes below."""
+    return [(0.5, (3.0 + 1e-3, 2e-3, 3e-3), (0.0, 0.2, 0.0)), (0.5, (-3.0 - 1e-3, 2e-3, 3e-3), (0.0, -0.2, 0.0))]
+
+
+def three_punctures(seed=2):
+    """m in {0.4, 0.3, 0.3} on an equilateral triangle of side 6 in z = 0,
+    in-plane momenta |P| <= 0.2 drawn by seed, zero spin."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i, m in enumerate((0.4, 0.3, 0.3)):
+        ang = np.pi / 2 + 2 * np.pi * i / 3
+        c = (6 / np.sqrt(3)) * np.array([np.cos(ang), np.sin(ang), 0.0]) + np.array([1e-3, 2e-3, 3e-3])
+        th = rng.uniform(0, 2 * np.pi)
+        mag = rng.uniform(0, 0.2)
+        out.append((m, tuple(c), (mag * np.cos(th), mag * np.sin(th), 0.0)))
+    return out
+
+
+def puncture_mesh(punctures, R=24.0, level=3, refine=2, p_base=4, p_fine=6):
+    """Box [-R, R]^3, cells within one cell width of a puncture refined `refine`
+    times (2:1 balanced); p_fine on the finest cells, p_base elsewhere."""
+    lo, hi = (-R, -R, -R), (R, R, R)
+    leaves = uniform_leaves(level)
+    cs = [np.asarray(c) for (_, c, _) in punctures]
+
+    def near(lf):
+        a, b = _cell_bounds(lf, lo, hi)
+        w = b[0] - a[0]
+        return any(_dist_range(a, b, c)[0] <= w for c in cs)
+
+    for _ in range(refine):
+        leaves = refine_(leaves, near)
+        leaves = balance_2to1(leaves)
+    leaves = morton_sort(leaves)
+    maxL = max(lf[0] for lf in leaves)
+    p = np.array([p_fine if lf[0] == maxL else p_base for lf in leaves], dtype=np.int32)
+    return dict(lo=lo, hi=hi, leaves=np.array(leaves, dtype=np.int32), p=p, warp=None)

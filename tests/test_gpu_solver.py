@@ -156,3 +156,30 @@ def test_solve_reports_not_converged(torch):
     st = ctx.solve(F, x, check=False, tol=1e-14, max_iter=2)
     assert st["status"] == dgell.DG_ERR_NOT_CONVERGED and st["iterations"] == 2
     ctx.close()
+
+
+def test_solve_graph_replay_matches_eager(torch):
+    """On a non-default stream dg_solve replays the V-cycle as a CUDA graph;
+    results are bit-identical to eager launches (deterministic kernels)."""
+    from paper_1907_01572_gb300 import dgell
+    desc, m, H = hierarchy("mixed_curved_2to1_l1")
+    b = inputs.random_vector(m.n_dofs, seed=21)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx = dgell.Context(desc)
+        bd = torch.tensor(b, device="cuda")
+        out = {}
+        for gm in (1, 0, 0):
+            for prec in (dgell.DG_FP64, dgell.DG_FP32):
+                x = torch.zeros_like(bd)
+                st = ctx.solve(bd, x, tol=1e-10, max_iter=300, mg_prec=prec, graph_mode=gm)
+                s.synchronize()
+                key = (gm, prec)
+                if key in out:
+                    assert torch.equal(out[key][0], x)
+                out[key] = (x.clone(), st["iterations"])
+        for prec in (dgell.DG_FP64, dgell.DG_FP32):
+            assert torch.equal(out[(1, prec)][0], out[(0, prec)][0])
+            assert out[(1, prec)][1] == out[(0, prec)][1]
+        ctx.close()
+    s.synchronize()
