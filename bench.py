@@ -213,6 +213,8 @@ def main():
         ms32 = timed(lambda: ctx.apply(x32, y32), args.steps, args.warmup)
     launches = (ctx.launch_count() - launches0) * args.steps // (args.steps + args.warmup)
     ms64 = timed(lambda: ctx.apply(x64, y64), max(3, args.steps // 4), args.warmup)
+    x16 = x64.bfloat16()
+    ms16 = timed(lambda: ctx.apply(x16, y32), args.steps, args.warmup)
 
     # end to end through the C ABI with host buffers (pinned), copies inside the region
     hx = x32.cpu().pin_memory()
@@ -227,10 +229,10 @@ def main():
 
     ms_e2e = timed(e2e_step, max(3, args.steps // 2), 2)
 
-    tms = torch.tensor([ms32, ms64, ms_e2e], device="cuda")
+    tms = torch.tensor([ms32, ms64, ms_e2e, ms16], device="cuda")
     if dist:
         dist.all_reduce(tms, op=dist.ReduceOp.MAX)
-    ms32, ms64, ms_e2e = [float(v) for v in tms.cpu()]
+    ms32, ms64, ms_e2e, ms16 = [float(v) for v in tms.cpu()]
     total_dofs = N * world
     g32 = total_dofs / (ms32 * 1e-3) / 1e9
     g64 = total_dofs / (ms64 * 1e-3) / 1e9
@@ -268,6 +270,10 @@ def main():
                                   "peak": peaks_alu.get("fp64"), "unit": "TFLOP/s",
                                   "frac": (flops / (ms64 * 1e-3) / 1e12) / peaks_alu["fp64"] if peaks_alu else None,
                                   "peak_kind": "measured this run: cuBLAS DGEMM 4096^3"}},
+            "bf16_operands": {"value": total_dofs / (ms16 * 1e-3) / 1e9, "unit": "GDOF/s", "ms_per_step": ms16,
+                              "bytes_per_dof": 18, "achieved_gbs": N * 18 / (ms16 * 1e-3) / 1e9,
+                              "frac_hbm": N * 18 / (ms16 * 1e-3) / 1e9 / hbm,
+                              "note": "x bf16, FP32 arithmetic, y fp32"},
             "fp32_alu": {"achieved": flops / (ms32 * 1e-3) / 1e12, "peak": peaks_alu.get("fp32"), "unit": "TFLOP/s",
                          "frac": (flops / (ms32 * 1e-3) / 1e12) / peaks_alu["fp32"] if peaks_alu else None,
                          "peak_kind": "measured this run: cuBLAS SGEMM 8192^3, TF32 off",

@@ -25,7 +25,8 @@
  *    stay valid until the work queued on the context's stream has finished.
  *    All device work is queued on the stream given at context creation.
  *  - Precision codes: DG_FP64 (double vectors, double arithmetic),
- *    DG_FP32 (float vectors, float arithmetic); DG_BF16 is reserved.
+ *    DG_FP32 (float vectors, float arithmetic), DG_BF16 (dg_apply only:
+ *    bfloat16 input vector, FP32 arithmetic, float output vector).
  */
 #ifndef DGELL_H
 #define DGELL_H
@@ -129,7 +130,8 @@ int dg_quadrature_points(dg_ctx* ctx, int level, double* vol_xyz, double* bnd_xy
  * matrix-free on level `level` (Sec. II.A.5, eq. harald-stiff; mortar
  * integrals with hp mortar projection, mortar figure).  x, y: device
  * vectors of the level's n_dofs in precision prec (double for DG_FP64,
- * float for DG_FP32); x and y must not overlap.  Asynchronous. */
+ * float for DG_FP32; DG_BF16: x bfloat16, y float); x and y must not
+ * overlap.  Asynchronous. */
 int dg_apply(dg_ctx* ctx, int level, int prec, const void* x, void* y);
 
 /* Right-hand side F_h of eq. (equationFh2) on the finest level:

@@ -16,4 +16,8 @@ template <typename T>
 cudaError_t launch_apply(const LevelView<T>& L, const BucketInfo* buckets, const T* x, T* y, cudaStream_t st,
                          int* launches);
 
+// BF16 operand x (2-byte bfloat16 values), FP32 arithmetic and FP32 y.
+cudaError_t launch_apply_bf16(const LevelView<float>& L, const BucketInfo* buckets, const void* x, float* y,
+                              cudaStream_t st, int* launches);
+
 }  // namespace dg

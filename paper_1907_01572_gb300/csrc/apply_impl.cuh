@@ -28,12 +28,21 @@
 // resident warps that shared memory and registers allow; face loops are
 // compiled per mortar size q; FP32 stages every mortar table in shared memory.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "apply.h"
 
 namespace dg {
 namespace apply_detail {
 
 constexpr int kQ = kMaxN;  // largest mortar q
+
+// Operand load: FP32 / FP64 vectors as stored, BF16 vectors widened to FP32.
+template <typename T, typename TX>
+__device__ __forceinline__ T ld(const TX* p) {
+    if constexpr (sizeof(TX) == 2) return (T)__bfloat162float(*p);
+    else return *p;
+}
 
 __device__ inline void tangential(int d, int& t1, int& t2) {
     t1 = d == 0 ? 1 : 0;
@@ -280,8 +289,8 @@ __device__ __forceinline__ T* load_tables(const LevelView<T>& L, const T*& sFT, 
     return sDL + N * N;
 }
 
-template <int N, typename T>
-__global__ void trace_kernel(LevelView<T> L, const int* __restrict__ bucket, int count, const T* __restrict__ x,
+template <int N, typename T, typename TX>
+__global__ void trace_kernel(LevelView<T> L, const int* __restrict__ bucket, int count, const TX* __restrict__ x,
                              T* __restrict__ mt) {
     using Ly = Layout<N>;
     constexpr int N3 = Ly::N3;
@@ -295,7 +304,7 @@ __global__ void trace_kernel(LevelView<T> L, const int* __restrict__ bucket, int
     for (int ei = blockIdx.x * nwarps + warp; ei < count; ei += gridDim.x * nwarps) {
         const int e = bucket[ei];
         const long long dofo = L.dof_off[e];
-        for (int k = lane; k < N3; k += 32) U[k] = x[dofo + k];
+        for (int k = lane; k < N3; k += 32) U[k] = ld<T>(x + dofo + k);
         __syncwarp();
         const int s0 = L.slot_off[e], s1 = L.slot_off[e + 1];
         for (int si = s0; si < s1; ++si) {
@@ -305,8 +314,8 @@ __global__ void trace_kernel(LevelView<T> L, const int* __restrict__ bucket, int
     }
 }
 
-template <int N, typename T>
-__global__ void element_kernel(LevelView<T> L, const int* __restrict__ bucket, int count, const T* __restrict__ x,
+template <int N, typename T, typename TX>
+__global__ void element_kernel(LevelView<T> L, const int* __restrict__ bucket, int count, const TX* __restrict__ x,
                                T* __restrict__ y) {
     using Ly = Layout<N>;
     constexpr int N2 = Ly::N2, N3 = Ly::N3;
@@ -328,7 +337,7 @@ __global__ void element_kernel(LevelView<T> L, const int* __restrict__ bucket, i
     for (int ei = blockIdx.x * nwarps + warp; ei < count; ei += gridDim.x * nwarps) {
         const int e = bucket[ei];
         const long long dofo = L.dof_off[e], vo = L.vqp_off[e];
-        for (int k = lane; k < N3; k += 32) U[k] = x[dofo + k];
+        for (int k = lane; k < N3; k += 32) U[k] = ld<T>(x + dofo + k);
         __syncwarp();
         wpass<N, 0, false, false>(U, A, sI, lane);
         __syncwarp();
@@ -432,35 +441,35 @@ inline int grid_cap() {
     return g;
 }
 
-template <int N, typename T>
-cudaError_t launch_trace(const LevelView<T>& L, const BucketInfo& b, const T* x, cudaStream_t st) {
+template <int N, typename T, typename TX>
+cudaError_t launch_trace(const LevelView<T>& L, const BucketInfo& b, const TX* x, cudaStream_t st) {
     using Ly = Layout<N>;
     static int W = 0, per_sm = 1;
     static size_t smem = 0;
     if (W == 0) {
         const size_t table_bytes = ((sizeof(T) == 4 ? ((L.ft.total + 3) & ~3) : 0) + 3 * N * N) * sizeof(T);
-        cudaError_t err = pick_warps(trace_kernel<N, T>, table_bytes, Ly::TWARP * sizeof(T), W, smem, per_sm);
+        cudaError_t err = pick_warps(trace_kernel<N, T, TX>, table_bytes, Ly::TWARP * sizeof(T), W, smem, per_sm);
         if (err != cudaSuccess) return err;
     }
     int grid = (b.count + W - 1) / W;
     if (grid > grid_cap() * per_sm) grid = grid_cap() * per_sm;
-    trace_kernel<N, T><<<grid, W * 32, smem, st>>>(L, b.elems, b.count, x, L.mt);
+    trace_kernel<N, T, TX><<<grid, W * 32, smem, st>>>(L, b.elems, b.count, x, L.mt);
     return cudaGetLastError();
 }
 
-template <int N, typename T>
-cudaError_t launch_element(const LevelView<T>& L, const BucketInfo& b, const T* x, T* y, cudaStream_t st) {
+template <int N, typename T, typename TX>
+cudaError_t launch_element(const LevelView<T>& L, const BucketInfo& b, const TX* x, T* y, cudaStream_t st) {
     using Ly = Layout<N>;
     static int W = 0, per_sm = 1;
     static size_t smem = 0;
     if (W == 0) {
         const size_t table_bytes = ((sizeof(T) == 4 ? ((L.ft.total + 3) & ~3) : 0) + 3 * N * N) * sizeof(T);
-        cudaError_t err = pick_warps(element_kernel<N, T>, table_bytes, Ly::EWARP * sizeof(T), W, smem, per_sm);
+        cudaError_t err = pick_warps(element_kernel<N, T, TX>, table_bytes, Ly::EWARP * sizeof(T), W, smem, per_sm);
         if (err != cudaSuccess) return err;
     }
     int grid = (b.count + W - 1) / W;
     if (grid > grid_cap() * per_sm) grid = grid_cap() * per_sm;
-    element_kernel<N, T><<<grid, W * 32, smem, st>>>(L, b.elems, b.count, x, y);
+    element_kernel<N, T, TX><<<grid, W * 32, smem, st>>>(L, b.elems, b.count, x, y);
     return cudaGetLastError();
 }
 
@@ -478,14 +487,14 @@ cudaError_t launch_element(const LevelView<T>& L, const BucketInfo& b, const T* 
 
 }  // namespace apply_detail
 
-template <typename T>
-cudaError_t launch_apply(const LevelView<T>& L, const BucketInfo* buckets, const T* x, T* y, cudaStream_t st,
-                         int* launches) {
+template <typename T, typename TX>
+cudaError_t launch_apply_x(const LevelView<T>& L, const BucketInfo* buckets, const TX* x, T* y, cudaStream_t st,
+                           int* launches) {
     for (int n = kMinN; n <= kMaxN; ++n) {   // every element's mortar traces first ...
         const BucketInfo& b = buckets[n];
         if (b.count == 0) continue;
         cudaError_t err = cudaSuccess;
-        DG_N_SWITCH(n, (err = apply_detail::launch_trace<NN, T>(L, b, x, st)))
+        DG_N_SWITCH(n, (err = apply_detail::launch_trace<NN, T, TX>(L, b, x, st)))
         if (err != cudaSuccess) return err;
         if (launches) ++*launches;
     }
@@ -493,11 +502,17 @@ cudaError_t launch_apply(const LevelView<T>& L, const BucketInfo* buckets, const
         const BucketInfo& b = buckets[n];
         if (b.count == 0) continue;
         cudaError_t err = cudaSuccess;
-        DG_N_SWITCH(n, (err = apply_detail::launch_element<NN, T>(L, b, x, y, st)))
+        DG_N_SWITCH(n, (err = apply_detail::launch_element<NN, T, TX>(L, b, x, y, st)))
         if (err != cudaSuccess) return err;
         if (launches) ++*launches;
     }
     return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_apply(const LevelView<T>& L, const BucketInfo* buckets, const T* x, T* y, cudaStream_t st,
+                         int* launches) {
+    return launch_apply_x<T, T>(L, buckets, x, y, st, launches);
 }
 
 }  // namespace dg

@@ -622,6 +622,12 @@ int dg_apply(dg_ctx* c, int level, int prec, const void* x, void* y) {
     if (x == y) return fail(DG_ERR_INVALID, "x and y must not alias");
     if (prec == DG_FP64) return apply_t<double>(c, level, (const double*)x, (double*)y);
     if (prec == DG_FP32) return apply_t<float>(c, level, (const float*)x, (float*)y);
+    if (prec == DG_BF16) {
+        int launches = 0;
+        CK(launch_apply_bf16(view<float>(c, level), c->lv[level].buckets, x, (float*)y, c->st, &launches));
+        c->launches += launches;
+        return DG_OK;
+    }
     return fail(DG_ERR_UNSUPPORTED, "precision not implemented");
 }
 

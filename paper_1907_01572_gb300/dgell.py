@@ -123,7 +123,9 @@ def _prec(t):
         return DG_FP64
     if t.dtype == torch.float32:
         return DG_FP32
-    raise ValueError("vectors must be float64 or float32")
+    if t.dtype == torch.bfloat16:
+        return DG_BF16
+    raise ValueError("vectors must be float64, float32 or bfloat16")
 
 
 def _stream():

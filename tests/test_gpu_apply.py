@@ -51,6 +51,13 @@ def test_apply_fp64_and_fp32(name, torch):
     ctx.apply(x32, y32)
     ref = A @ x32.double().cpu().numpy()
     assert rel_l2(y32.double().cpu().numpy(), ref) < 1e-5
+    # BF16 operands, FP32 arithmetic: exact-input parity 1e-5, and within 2e-3
+    # of the FP64 operator applied to the unrounded input
+    x16 = xd.bfloat16()
+    y16 = torch.empty(m.n_dofs, dtype=torch.float32, device="cuda")
+    ctx.apply(x16, y16)
+    assert rel_l2(y16.double().cpu().numpy(), A @ x16.double().cpu().numpy()) < 1e-5
+    assert rel_l2(y16.double().cpu().numpy(), A @ x) < 2e-3
     # repeat: deterministic, bit-identical
     y2 = torch.empty_like(xd)
     ctx.apply(xd, y2)
