@@ -357,6 +357,14 @@ def solve_bench(dgell, inputs, torch, n_solves=8):
         out["two_puncture_newton"] = res
         ctx.close()
     stream.synchronize()
+    # served workload: requests of mixed type and size arriving as a Poisson process,
+    # admitted by footprint onto 4 worker streams (FP32 V-cycle, FP64 outer, 1e-10)
+    from paper_1907_01572_gb300 import serve
+    reqs = serve.make_requests(n=24, rate_hz=10.0, seed=2)
+    _, summary = serve.Server(slots=4).run(reqs)
+    summary["workload"] = ("24 requests, Poisson arrivals 10/s; mix of Poisson (4^3-8^3 elements, p 3..5), "
+                           "star (density jump) and two-puncture Newton solves, seed 2")
+    out["served"] = summary
     return out
 
 
