@@ -116,6 +116,21 @@ print(json.dumps({"dofs": dofs, "seconds": dt}))
     return d["dofs"] / d["seconds"] / 1e9, d["dofs"], d["seconds"]
 
 
+def max_over_ranks(values, dist, device):
+    """Per-step times reduced with MAX over the ranks of the replica job (no
+    data-path collective: each rank applies its own copy of the operator)."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def job_throughput(dofs_per_rank, world, ms_max):
+    """Whole-job GDOF/s: DOFs applied by all ranks / the slowest rank's time."""
+    return dofs_per_rank * world / (ms_max * 1e-3) / 1e9
+
+
 WORKLOAD = "operator-apply sweep: 32^3 hex on [-1,1]^3, octant x,y,z<0 h-refined 2:1 (61440 elems), " \
            "p~U{2..7} seed 0, sine-warped isoparametric geometry, x~N(0,1) seed 1"
 
@@ -229,14 +244,11 @@ def main():
 
     ms_e2e = timed(e2e_step, max(3, args.steps // 2), 2)
 
-    tms = torch.tensor([ms32, ms64, ms_e2e, ms16], device="cuda")
-    if dist:
-        dist.all_reduce(tms, op=dist.ReduceOp.MAX)
-    ms32, ms64, ms_e2e, ms16 = [float(v) for v in tms.cpu()]
+    ms32, ms64, ms_e2e, ms16 = max_over_ranks([ms32, ms64, ms_e2e, ms16], dist, "cuda")
     total_dofs = N * world
-    g32 = total_dofs / (ms32 * 1e-3) / 1e9
-    g64 = total_dofs / (ms64 * 1e-3) / 1e9
-    ge2e = total_dofs / (ms_e2e * 1e-3) / 1e9
+    g32 = job_throughput(N, world, ms32)
+    g64 = job_throughput(N, world, ms64)
+    ge2e = job_throughput(N, world, ms_e2e)
 
     # algorithmic bytes per DOF: x + y + 3 coordinates per LGL node (curved isoparametric geometry)
     b32 = 4 + 4 + 12

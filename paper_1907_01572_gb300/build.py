@@ -29,7 +29,8 @@ def sources():
 def build(verbose=False, force=False):
     os.makedirs(BUILD, exist_ok=True)
     srcs = sources()
-    deps = srcs + glob.glob(os.path.join(CSRC, "*.h")) + [os.path.join(HERE, "..", "include", "dgell.h")]
+    deps = (srcs + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
+            + [os.path.join(HERE, "..", "include", "dgell.h")])
     newest = max(os.path.getmtime(p) for p in deps)
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB

@@ -30,6 +30,8 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "apply.h"
 
 namespace dg {
@@ -290,8 +292,8 @@ __device__ __forceinline__ T* load_tables(const LevelView<T>& L, const T*& sFT, 
 }
 
 template <int N, typename T, typename TX>
-__global__ void trace_kernel(LevelView<T> L, const int* __restrict__ bucket, int count, const TX* __restrict__ x,
-                             T* __restrict__ mt) {
+__device__ __forceinline__ void trace_body(const LevelView<T>& L, const int* __restrict__ bucket, int count,
+                                           const TX* __restrict__ x, T* __restrict__ mt, int blk, int nblk) {
     using Ly = Layout<N>;
     constexpr int N3 = Ly::N3;
     const T* sFT;
@@ -301,7 +303,7 @@ __global__ void trace_kernel(LevelView<T> L, const int* __restrict__ bucket, int
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T* U = wbase + warp * Ly::TWARP;
     T* F = U + N3;
-    for (int ei = blockIdx.x * nwarps + warp; ei < count; ei += gridDim.x * nwarps) {
+    for (int ei = blk * nwarps + warp; ei < count; ei += nblk * nwarps) {
         const int e = bucket[ei];
         const long long dofo = L.dof_off[e];
         for (int k = lane; k < N3; k += 32) U[k] = ld<T>(x + dofo + k);
@@ -315,8 +317,14 @@ __global__ void trace_kernel(LevelView<T> L, const int* __restrict__ bucket, int
 }
 
 template <int N, typename T, typename TX>
-__global__ void element_kernel(LevelView<T> L, const int* __restrict__ bucket, int count, const TX* __restrict__ x,
-                               T* __restrict__ y) {
+__global__ void trace_kernel(LevelView<T> L, const int* __restrict__ bucket, int count, const TX* __restrict__ x,
+                             T* __restrict__ mt) {
+    trace_body<N, T, TX>(L, bucket, count, x, mt, blockIdx.x, gridDim.x);
+}
+
+template <int N, typename T, typename TX>
+__device__ __forceinline__ void element_body(const LevelView<T>& L, const int* __restrict__ bucket, int count,
+                                             const TX* __restrict__ x, T* __restrict__ y, int blk, int nblk) {
     using Ly = Layout<N>;
     constexpr int N2 = Ly::N2, N3 = Ly::N3;
     const T* sFT;
@@ -334,7 +342,7 @@ __global__ void element_kernel(LevelView<T> L, const int* __restrict__ bucket, i
     T* F = Ly::ALIAS ? A : G3 + N3;
     const bool mass = L.c0 != nullptr;
     (void)N2;
-    for (int ei = blockIdx.x * nwarps + warp; ei < count; ei += gridDim.x * nwarps) {
+    for (int ei = blk * nwarps + warp; ei < count; ei += nblk * nwarps) {
         const int e = bucket[ei];
         const long long dofo = L.dof_off[e], vo = L.vqp_off[e];
         for (int k = lane; k < N3; k += 32) U[k] = ld<T>(x + dofo + k);
@@ -397,6 +405,55 @@ __global__ void element_kernel(LevelView<T> L, const int* __restrict__ bucket, i
         for (int k = lane; k < N3; k += 32) y[dofo + k] = Y[k];
         __syncwarp();
     }
+}
+
+template <int N, typename T, typename TX>
+__global__ void element_kernel(LevelView<T> L, const int* __restrict__ bucket, int count, const TX* __restrict__ x,
+                               T* __restrict__ y) {
+    element_body<N, T, TX>(L, bucket, count, x, y, blockIdx.x, gridDim.x);
+}
+
+// All degree buckets of a level in one launch (used on small levels, where
+// launch latency rather than bandwidth bounds the apply): CTA ranges map to
+// buckets; each CTA runs the body compiled for its bucket's degree.
+struct FusedBuckets {
+    int nb;
+    int n[kNumN];
+    const int* elems[kNumN];
+    int count[kNumN];
+    int cta_start[kNumN + 1];
+};
+
+#define DG_BODY_SWITCH(NV, CALL)                           \
+    switch (NV) {                                          \
+        case 2: { constexpr int NN = 2; CALL; break; }     \
+        case 3: { constexpr int NN = 3; CALL; break; }     \
+        case 4: { constexpr int NN = 4; CALL; break; }     \
+        case 5: { constexpr int NN = 5; CALL; break; }     \
+        case 6: { constexpr int NN = 6; CALL; break; }     \
+        case 7: { constexpr int NN = 7; CALL; break; }     \
+        case 8: { constexpr int NN = 8; CALL; break; }     \
+        default: { constexpr int NN = 9; CALL; break; }    \
+    }
+
+__device__ __forceinline__ int fused_bucket(const FusedBuckets& fb) {
+    int b = 0;
+    while (b + 1 < fb.nb && (int)blockIdx.x >= fb.cta_start[b + 1]) ++b;
+    return b;
+}
+
+template <typename T, typename TX>
+__global__ void trace_fused(LevelView<T> L, FusedBuckets fb, const TX* __restrict__ x, T* __restrict__ mt) {
+    const int b = fused_bucket(fb);
+    const int blk = blockIdx.x - fb.cta_start[b], nblk = fb.cta_start[b + 1] - fb.cta_start[b];
+    DG_BODY_SWITCH(fb.n[b], (trace_body<NN, T, TX>(L, fb.elems[b], fb.count[b], x, mt, blk, nblk)))
+}
+
+template <typename T, typename TX>
+__global__ void element_fused(LevelView<T> L, FusedBuckets fb, const TX* __restrict__ x, T* __restrict__ y) {
+    const int b = fused_bucket(fb);
+    const int blk = blockIdx.x - fb.cta_start[b], nblk = fb.cta_start[b + 1] - fb.cta_start[b];
+    DG_BODY_SWITCH(fb.n[b], (element_body<NN, T, TX>(L, fb.elems[b], fb.count[b], x, y, blk, nblk)))
 }
 
 inline int& sm_count() {
@@ -487,9 +544,67 @@ cudaError_t launch_element(const LevelView<T>& L, const BucketInfo& b, const TX*
 
 }  // namespace apply_detail
 
+namespace apply_detail {
+
+constexpr int kFusedWarps = 8;
+constexpr int kFusedMaxElems = 8192;   // levels up to this size use the single-launch path
+
+template <typename T, typename TX>
+cudaError_t launch_fused(const LevelView<T>& L, const BucketInfo* buckets, const TX* x, T* y, cudaStream_t st,
+                         int* launches) {
+    const size_t cap = 220 * 1024;
+    const size_t table_vals_base = (sizeof(T) == 4 ? ((L.ft.total + 3) & ~3) : 0);
+    size_t max_tw = 0, max_ew = 0, max_tv = 0;
+    for (int n = kMinN; n <= kMaxN; ++n) {
+        if (buckets[n].count == 0) continue;
+        size_t tw = 0, ew = 0;
+        DG_N_SWITCH(n, (tw = Layout<NN>::TWARP, ew = Layout<NN>::EWARP))
+        max_tw = std::max(max_tw, tw);
+        max_ew = std::max(max_ew, ew);
+        max_tv = std::max(max_tv, table_vals_base + 3 * (size_t)n * n);
+    }
+    if (max_ew == 0) return cudaSuccess;
+    int W = kFusedWarps;   // same CTA shape for every bucket; shrink until the largest degree fits
+    while (W > 1 && (max_tv + (size_t)W * std::max(max_tw, max_ew)) * sizeof(T) > cap) --W;
+    const size_t smem_t = (max_tv + (size_t)W * max_tw) * sizeof(T);
+    const size_t smem_e = (max_tv + (size_t)W * max_ew) * sizeof(T);
+    FusedBuckets fb{};
+    int ctas = 0;
+    for (int n = kMinN; n <= kMaxN; ++n) {
+        const BucketInfo& b = buckets[n];
+        if (b.count == 0) continue;
+        fb.n[fb.nb] = n;
+        fb.elems[fb.nb] = b.elems;
+        fb.count[fb.nb] = b.count;
+        fb.cta_start[fb.nb] = ctas;
+        ctas += (b.count + W - 1) / W;
+        ++fb.nb;
+    }
+    fb.cta_start[fb.nb] = ctas;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e1 = cudaFuncSetAttribute(trace_fused<T, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+        cudaError_t e2 = cudaFuncSetAttribute(element_fused<T, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+        if (e1 != cudaSuccess) return e1;
+        if (e2 != cudaSuccess) return e2;
+        attr = true;
+    }
+    trace_fused<T, TX><<<ctas, W * 32, smem_t, st>>>(L, fb, x, L.mt);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    element_fused<T, TX><<<ctas, W * 32, smem_e, st>>>(L, fb, x, y);
+    err = cudaGetLastError();
+    if (launches) *launches += 2;
+    return err;
+}
+
+}  // namespace apply_detail
+
 template <typename T, typename TX>
 cudaError_t launch_apply_x(const LevelView<T>& L, const BucketInfo* buckets, const TX* x, T* y, cudaStream_t st,
                            int* launches) {
+    if (L.n_elems <= apply_detail::kFusedMaxElems)
+        return apply_detail::launch_fused<T, TX>(L, buckets, x, y, st, launches);
     for (int n = kMinN; n <= kMaxN; ++n) {   // every element's mortar traces first ...
         const BucketInfo& b = buckets[n];
         if (b.count == 0) continue;

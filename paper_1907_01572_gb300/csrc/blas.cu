@@ -81,6 +81,16 @@ __global__ void sm_init_kernel(SmState* s, const double* rr) {
     s->skip = 0;
 }
 
+__device__ void alpha_logic(SmState* s, double v) {
+    s->pAp = v;
+    if (s->stop || !(v > 0.0) || !(s->rr > 0.0) || !isfinite(v)) {
+        s->stop = 1;
+        s->a = 0.0;
+        return;
+    }
+    s->a = s->rr / v;
+}
+
 __global__ void sm_alpha_kernel(SmState* s, const double* pAp) {
     const double v = pAp[0];
     s->pAp = v;
@@ -113,6 +123,72 @@ __global__ void cg_xr_kernel(const SmState* s, T* x, T* r, const T* p, const T* 
 // Gershgorin bound of row k of the Lanczos tridiagonal built from the CG
 // coefficients (Alg. 5, eq. tridiag): T_kk = 1/a_k + b_{k-1}/a_{k-1},
 // |T_k,k-1| = sqrt(b_{k-1})/a_{k-1}, |T_k,k+1| = sqrt(b_k)/a_k.
+__device__ void beta_logic(SmState* s, double rn) {
+    if (s->stop) return;
+    const double beta = rn / s->rr;
+    s->beta = beta;
+    s->rr = rn;
+    double diag = 1.0 / s->a, left = 0.0;
+    if (s->have_prev) {
+        diag += s->b_prev / s->a_prev;
+        left = sqrt(s->b_prev) / s->a_prev;
+    }
+    const double lk = diag + left + sqrt(beta) / s->a;
+    if (isfinite(lk) && lk > s->lam) s->lam = lk;
+    s->a_prev = s->a;
+    s->b_prev = beta;
+    s->have_prev = 1;
+}
+
+// Last block of a grid: sums partials[i * 4] over the grid's blocks in index order.
+__device__ bool last_block_sum(double* partials, unsigned* counter, double* sh, double& total) {
+    __shared__ bool last;
+    __threadfence();
+    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double v = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) v += ((volatile double*)partials)[i * 4];
+    total = block_sum(v, sh);
+    if (threadIdx.x == 0) *counter = 0u;
+    return true;
+}
+
+template <typename T>
+__global__ void cg_alpha_fused_kernel(SmState* s, const T* p, const T* Ap, long long n, double* partials,
+                                      unsigned* counter) {
+    __shared__ double sh[kRedThreads];
+    double v = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        v += (double)p[i] * (double)Ap[i];
+    const double b = block_sum(v, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x * 4] = b;
+    double total;
+    if (last_block_sum(partials, counter, sh, total) && threadIdx.x == 0) alpha_logic(s, total);
+}
+
+template <typename T>
+__global__ void cg_update_fused_kernel(SmState* s, T* x, T* r, const T* p, const T* Ap, long long n,
+                                       double* partials, unsigned* counter) {
+    __shared__ double sh[kRedThreads];
+    const bool stop = s->stop != 0;
+    const T a = (T)s->a;
+    double v = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        if (!stop) {
+            x[i] += a * p[i];
+            const T ri = r[i] - a * Ap[i];
+            r[i] = ri;
+            v += (double)ri * (double)ri;
+        }
+    }
+    const double b = block_sum(v, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x * 4] = b;
+    double total;
+    if (last_block_sum(partials, counter, sh, total) && threadIdx.x == 0) beta_logic(s, total);
+}
+
 __global__ void sm_beta_kernel(SmState* s, const double* rr_new) {
     if (s->stop) return;
     const double rn = rr_new[0];
@@ -290,6 +366,24 @@ cudaError_t sm_init(SmState* s, const double* rr, cudaStream_t st) {
     sm_init_kernel<<<1, 1, 0, st>>>(s, rr);
     return cudaGetLastError();
 }
+template <typename T>
+cudaError_t cg_alpha_fused(SmState* s, const T* p, const T* Ap, long long n, Red red, cudaStream_t st) {
+    cg_alpha_fused_kernel<T><<<kRedBlocks, kRedThreads, 0, st>>>(s, p, Ap, n, red.partials, red.counter);
+    return cudaGetLastError();
+}
+template cudaError_t cg_alpha_fused<double>(SmState*, const double*, const double*, long long, Red, cudaStream_t);
+template cudaError_t cg_alpha_fused<float>(SmState*, const float*, const float*, long long, Red, cudaStream_t);
+
+template <typename T>
+cudaError_t cg_update_fused(SmState* s, T* x, T* r, const T* p, const T* Ap, long long n, Red red, cudaStream_t st) {
+    cg_update_fused_kernel<T><<<kRedBlocks, kRedThreads, 0, st>>>(s, x, r, p, Ap, n, red.partials, red.counter);
+    return cudaGetLastError();
+}
+template cudaError_t cg_update_fused<double>(SmState*, double*, double*, const double*, const double*, long long, Red,
+                                             cudaStream_t);
+template cudaError_t cg_update_fused<float>(SmState*, float*, float*, const float*, const float*, long long, Red,
+                                            cudaStream_t);
+
 cudaError_t sm_alpha(SmState* s, const double* pAp, cudaStream_t st) {
     sm_alpha_kernel<<<1, 1, 0, st>>>(s, pAp);
     return cudaGetLastError();

@@ -24,6 +24,7 @@ struct FcgState {       // flexible-CG scalars (device)
 struct Red {            // reduction scratch: partials[kRedBlocks * 4] + results[4]
     double* partials;
     double* out;
+    unsigned* counter;  // blocks done, for the single-launch (last block) reductions; 0 between launches
 };
 
 // out[0..k) = dot products of (a_i, b_i) pairs, T in {float, double}, accumulated in double.
@@ -39,6 +40,13 @@ cudaError_t residual_init(const T* b, const T* y, T* r, T* p, long long n, Red r
 
 // CGEIGS pieces
 cudaError_t sm_init(SmState* s, const double* rr, cudaStream_t st);
+// Fused CG step, two launches plus the p update: (1) p.Ap and alpha, (2) x, r
+// update with r.r, beta and the Gershgorin bound; the last block to finish
+// sums the per-block partials in index order (same result as dots + finalize).
+template <typename T>
+cudaError_t cg_alpha_fused(SmState* s, const T* p, const T* Ap, long long n, Red red, cudaStream_t st);
+template <typename T>
+cudaError_t cg_update_fused(SmState* s, T* x, T* r, const T* p, const T* Ap, long long n, Red red, cudaStream_t st);
 cudaError_t sm_alpha(SmState* s, const double* pAp, cudaStream_t st);
 template <typename T>
 cudaError_t cg_xr_update(const SmState* s, T* x, T* r, const T* p, const T* Ap, long long n, Red red, cudaStream_t st);

@@ -159,14 +159,10 @@ int smooth_t(dg_ctx* c, int l, const T* b, T* x, const dg_cheb_opts* o) {
     c->launches += 3;
     for (int k = 0; k < ne; ++k) {
         if ((rc = apply_t<T>(c, l, W.p, W.Ap))) return rc;
-        const T* a[1] = {W.p};
-        const T* bb[1] = {W.Ap};
-        CK(dots<T>(a, bb, 1, n, c->red, st));
-        CK(sm_alpha(W.sm, c->red.out, st));
-        CK(cg_xr_update<T>(W.sm, x, W.r, W.p, W.Ap, n, c->red, st));
-        CK(sm_beta(W.sm, c->red.out, st));
+        CK(cg_alpha_fused<T>(W.sm, W.p, W.Ap, n, c->red, st));
+        CK(cg_update_fused<T>(W.sm, x, W.r, W.p, W.Ap, n, c->red, st));
         CK(cg_p_update<T>(W.sm, W.p, W.r, n, st));
-        c->launches += 7;
+        c->launches += 3;
     }
     CK(sm_cheb_coeffs(W.sm, nc, Lam, st));
     CK(cudaMemsetAsync(W.p, 0, n * sizeof(T), st));
@@ -531,6 +527,8 @@ int dg_ctx_create(const dg_mesh_desc* mesh, const dg_disc_opts* opts, void* stre
     c->ftab32 = c->arena.upload(ftabf, c->st);
     c->red.partials = c->arena.alloc<double>(kRedBlocks * 4);
     c->red.out = c->arena.alloc<double>(4);
+    c->red.counter = c->arena.alloc<unsigned>(1);
+    if (c->red.counter) cudaMemsetAsync(c->red.counter, 0, sizeof(unsigned), c->st);
     c->fcg = c->arena.alloc<FcgState>(1);
     if (c->arena.failed) {
         c->arena.free_all();

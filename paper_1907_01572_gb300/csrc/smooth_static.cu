@@ -30,7 +30,7 @@ namespace {
 constexpr long long kStaticMaxDofs = 1LL << 18;   // 262,144 DOFs per level
 constexpr size_t kVecBytes = (size_t)kStaticMaxDofs * sizeof(double);
 constexpr size_t kStateBytes = (sizeof(SmState) + 255) / 256 * 256;
-constexpr size_t kRedBytes = ((size_t)(kRedBlocks * 4 + 4) * sizeof(double) + 255) / 256 * 256;
+constexpr size_t kRedBytes = ((size_t)(kRedBlocks * 4 + 4 + 1) * sizeof(double) + 255) / 256 * 256;
 constexpr size_t kStaticBytes = 3 * kVecBytes + kStateBytes + kRedBytes;   // ~6.1 MB
 
 static __device__ __align__(256) unsigned char g_smooth_scratch[kStaticBytes];
@@ -112,8 +112,9 @@ int smooth_static_t(dg_ctx* c, int l, const T* b, T* x, const dg_cheb_opts* o, u
     T* p = reinterpret_cast<T*>(base + kVecBytes);
     T* Ap = reinterpret_cast<T*>(base + 2 * kVecBytes);
     SmState* sm = reinterpret_cast<SmState*>(base + 3 * kVecBytes);
-    Red red{reinterpret_cast<double*>(base + 3 * kVecBytes + kStateBytes), nullptr};
+    Red red{reinterpret_cast<double*>(base + 3 * kVecBytes + kStateBytes), nullptr, nullptr};
     red.out = red.partials + kRedBlocks * 4;
+    red.counter = reinterpret_cast<unsigned*>(red.out + 4);   // zero at load; each last block resets it
     cudaStream_t st = c->st;
     const LevelView<T> view = static_view<T>(c, l);
     int launches = 0;
@@ -122,12 +123,8 @@ int smooth_static_t(dg_ctx* c, int l, const T* b, T* x, const dg_cheb_opts* o, u
     CKS(sm_init(sm, red.out, st));
     for (int k = 0; k < ne; ++k) {
         CKS(launch_apply<T>(view, c->lv[l].buckets, p, Ap, st, &launches));
-        const T* a[1] = {p};
-        const T* bb[1] = {Ap};
-        CKS(dots<T>(a, bb, 1, n, red, st));
-        CKS(sm_alpha(sm, red.out, st));
-        CKS(cg_xr_update<T>(sm, x, r, p, Ap, n, red, st));
-        CKS(sm_beta(sm, red.out, st));
+        CKS(cg_alpha_fused<T>(sm, p, Ap, n, red, st));
+        CKS(cg_update_fused<T>(sm, x, r, p, Ap, n, red, st));
         CKS(cg_p_update<T>(sm, p, r, n, st));
     }
     CKS(sm_cheb_coeffs(sm, nc, Lam, st));
@@ -136,7 +133,7 @@ int smooth_static_t(dg_ctx* c, int l, const T* b, T* x, const dg_cheb_opts* o, u
         CKS(launch_apply<T>(view, c->lv[l].buckets, x, Ap, st, &launches));
         CKS(cheb_step<T>(sm, k, b, Ap, p, x, n, st));
     }
-    c->launches += launches + 3 + 7 * ne + 1 + nc;
+    c->launches += launches + 3 + 3 * ne + 1 + nc;
     return DG_OK;
 }
 
