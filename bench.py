@@ -22,6 +22,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 HBM_FALLBACK = 6800.0
+# ncu DRAM bytes (read + write) of one FP32 apply of the sweep mesh, measured for the
+# kernels of library version 104 (profiles/apply_sweep32_traffic_v4.md); null for other versions.
+TRAFFIC_BYTES_PER_APPLY = {104: 1.3634e9}
 
 
 def peaks():
@@ -270,8 +273,9 @@ def main():
             "config": {"workload": WORKLOAD, "n_dofs": N, "n_elems": info["n_elems"], "levels": info["n_levels"],
                        "l2": "inputs larger than L2 (x, y, metric terms ~0.6 GB)", "parallelism": "replicas"},
             "roofline": {"bound": "hbm", "achieved": ach32, "peak": hbm, "unit": "GB/s", "frac": ach32 / hbm,
-                         "traffic": None, "peak_kind": peak_kind,
-                         "bytes_per_dof": b32, "kernel": "apply_kernel (all degree buckets, one apply)"},
+                         "traffic": TRAFFIC_BYTES_PER_APPLY.get(dgell.dg_version()) if args.level == 5 else None,
+                         "peak_kind": peak_kind, "bytes_per_dof": b32,
+                         "kernel": "dg_apply FP32: trace + element kernels of all degree buckets (one apply)"},
             "cpu_baseline": cpu,
             "e2e": {"value": ge2e, "unit": "GDOF/s", "h2d_bytes_per_step": N * 4, "d2h_bytes_per_step": N * 4},
             "gpu_launches": int(launches),

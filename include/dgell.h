@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define DGELL_VERSION 100
+#define DGELL_VERSION 104
 
 enum {
     DG_OK = 0,

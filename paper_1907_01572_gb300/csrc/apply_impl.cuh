@@ -547,7 +547,7 @@ cudaError_t launch_element(const LevelView<T>& L, const BucketInfo& b, const TX*
 namespace apply_detail {
 
 constexpr int kFusedWarps = 8;
-constexpr int kFusedMaxElems = 8192;   // levels up to this size use the single-launch path
+constexpr int kFusedMaxElems = 1216;   // 152 SMs x 8 warps: levels this small use the single-launch path
 
 template <typename T, typename TX>
 cudaError_t launch_fused(const LevelView<T>& L, const BucketInfo* buckets, const TX* x, T* y, cudaStream_t st,

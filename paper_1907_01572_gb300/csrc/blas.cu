@@ -323,6 +323,47 @@ __global__ void dense_matvec_kernel(const double* M, const T* x, T* y, int n) {
     }
 }
 
+// Column-major y = M x: a block of 256 threads owns 32 rows and splits the
+// columns into 8 slices (fixed order, so the result is reproducible).
+template <typename T>
+__global__ void dense_matvec_t_kernel(const T* M, const T* x, T* y, int n) {
+    __shared__ T part[8][32];
+    const int row = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int slice = threadIdx.x >> 5;
+    T s = 0;
+    if (row < n)
+        for (int j = slice; j < n; j += 8) s += M[(long long)j * n + row] * x[j];
+    part[slice][threadIdx.x & 31] = s;
+    __syncthreads();
+    if (slice == 0 && row < n) {
+        T t = 0;
+        for (int k = 0; k < 8; ++k) t += part[k][threadIdx.x];
+        y[row] = t;
+    }
+}
+
+__global__ void dense_copy_kernel(const double* L, double* D, long long nn) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn; i += (long long)gridDim.x * blockDim.x)
+        D[i] = L[i];
+}
+
+__global__ void dense_blocks_kernel(const double* Ob, const long long* Ob_off, const long long* dof_off, const int* p,
+                                    int n, double* D) {
+    const int e = blockIdx.x;
+    const int ne = p[e] + 1, n3 = ne * ne * ne;
+    const double* Oe = Ob + Ob_off[e];
+    const long long o = dof_off[e];
+    for (int k = threadIdx.x; k < n3 * n3; k += blockDim.x) {
+        const int j = k / n3, i = k % n3;
+        D[(o + j) * n + (o + i)] += Oe[k];
+    }
+}
+
+__global__ void dense_cast_kernel(const double* D, float* D32, long long nn) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn; i += (long long)gridDim.x * blockDim.x)
+        D32[i] = (float)D[i];
+}
+
 inline int grid_for(long long n) {
     long long g = (n + 255) / 256;
     return (int)(g < 1 ? 1 : (g > 4 * 152 * 4 ? 4 * 152 * 4 : g));
@@ -459,6 +500,23 @@ cudaError_t dense_matvec(const double* M, const T* x, T* y, int n, cudaStream_t 
     return cudaGetLastError();
 }
 template cudaError_t dense_matvec<double>(const double*, const double*, double*, int, cudaStream_t);
+
+cudaError_t dense_compose(const double* Lmat, const double* Ob, const long long* Ob_off, const long long* dof_off,
+                          const int* p, int n_elems, int n, double* D, float* D32, cudaStream_t st) {
+    const long long nn = (long long)n * n;
+    dense_copy_kernel<<<grid_for(nn), 256, 0, st>>>(Lmat, D, nn);
+    if (Ob) dense_blocks_kernel<<<n_elems, 256, 0, st>>>(Ob, Ob_off, dof_off, p, n, D);
+    dense_cast_kernel<<<grid_for(nn), 256, 0, st>>>(D, D32, nn);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t dense_matvec_t(const T* M, const T* x, T* y, int n, cudaStream_t st) {
+    dense_matvec_t_kernel<T><<<(n + 31) / 32, 256, 0, st>>>(M, x, y, n);
+    return cudaGetLastError();
+}
+template cudaError_t dense_matvec_t<double>(const double*, const double*, double*, int, cudaStream_t);
+template cudaError_t dense_matvec_t<float>(const float*, const float*, float*, int, cudaStream_t);
 template cudaError_t dense_matvec<float>(const double*, const float*, float*, int, cudaStream_t);
 
 }  // namespace dg

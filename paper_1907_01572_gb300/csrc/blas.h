@@ -73,5 +73,12 @@ cudaError_t sub3(const T* a, const T* b, T* c, long long n, cudaStream_t st);  /
 // y = M x, M dense n x n (double, column-major), T vectors
 template <typename T>
 cudaError_t dense_matvec(const double* M, const T* x, T* y, int n, cudaStream_t st);
+// D = L + blockdiag(O_e) (column-major n x n; O_e column-major (n_e^3)^2 at Ob_off[e]),
+// D32 = (float) D
+cudaError_t dense_compose(const double* Lmat, const double* Ob, const long long* Ob_off, const long long* dof_off,
+                          const int* p, int n_elems, int n, double* D, float* D32, cudaStream_t st);
+// y = M x with M in the vectors' precision (column-major)
+template <typename T>
+cudaError_t dense_matvec_t(const T* M, const T* x, T* y, int n, cudaStream_t st);
 
 }  // namespace dg

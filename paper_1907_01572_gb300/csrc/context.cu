@@ -118,6 +118,69 @@ int apply_t(dg_ctx* c, int l, const T* x, T* y) {
     return DG_OK;
 }
 
+// Small coarse levels (at most kDenseMax DOFs): the solver applies the
+// assembled operator as a dense matrix-vector product -- one launch instead of
+// the latency-bound element pipeline.  The SIPG part is assembled once per
+// context, column by column with the matrix-free FP64 apply; the Galerkin
+// zeroth-order blocks are added whenever the operator's coefficients change.
+// dg_apply itself always stays matrix-free.
+constexpr long long kDenseMax = 1024;
+
+int ensure_dense(dg_ctx* c, int l) {
+    LevelDev& L = c->lv[l];
+    const long long n = L.h.n_dofs();
+    if (n > kDenseMax || l == (int)c->lv.size() - 1) return DG_OK;
+    if (L.dense64 && L.dense_version == c->op_version) return DG_OK;
+    if (!L.denseL) {
+        L.denseL = c->arena.alloc<double>((size_t)n * n);
+        L.dense64 = c->arena.alloc<double>((size_t)n * n);
+        L.dense32 = c->arena.alloc<float>((size_t)n * n);
+        if (c->arena.failed) return fail(DG_ERR_OOM, "device allocation failed (small-level operator)");
+        double* E = nullptr;
+        CK(cudaMalloc(&E, sizeof(double) * n * n));
+        std::vector<double> eye((size_t)n * n, 0.0);
+        for (long long j = 0; j < n; ++j) eye[(size_t)j * n + j] = 1.0;
+        CK(cudaMemcpyAsync(E, eye.data(), sizeof(double) * eye.size(), cudaMemcpyHostToDevice, c->st));
+        const bool z = L.z_active;
+        L.z_active = false;   // SIPG part only (restored below; not an argument change of any graph)
+        for (long long j = 0; j < n; ++j) {
+            int rc = apply_t<double>(c, l, E + j * n, L.denseL + j * n);
+            if (rc) {
+                L.z_active = z;
+                cudaFree(E);
+                return rc;
+            }
+        }
+        L.z_active = z;
+        CK(cudaStreamSynchronize(c->st));
+        cudaFree(E);
+    }
+    const bool blocks = L.z_active && L.Ob64;
+    CK(dense_compose(L.denseL, blocks ? L.Ob64 : nullptr, L.Ob_off, L.dof_off, L.p, L.h.n_elems(), (int)n, L.dense64,
+                     L.dense32, c->st));
+    c->launches += blocks ? 3 : 2;
+    L.dense_version = c->op_version;
+    return DG_OK;
+}
+
+template <typename T>
+const T* dense_of(LevelDev& L);
+template <>
+const double* dense_of<double>(LevelDev& L) { return L.dense64; }
+template <>
+const float* dense_of<float>(LevelDev& L) { return L.dense32; }
+
+template <typename T>
+int solver_apply(dg_ctx* c, int l, const T* x, T* y) {
+    LevelDev& L = c->lv[l];
+    if (L.dense64 && L.dense_version == c->op_version) {
+        CK(dense_matvec_t<T>(dense_of<T>(L), x, y, (int)L.h.n_dofs(), c->st));
+        c->launches += 1;
+        return DG_OK;
+    }
+    return apply_t<T>(c, l, x, y);
+}
+
 template <typename T>
 int ensure_work(dg_ctx* c, int l) {
     Work<T>& W = work_of<T>(c->lv[l]);
@@ -147,18 +210,19 @@ template <typename T>
 int smooth_t(dg_ctx* c, int l, const T* b, T* x, const dg_cheb_opts* o) {
     int rc = ensure_work<T>(c, l);
     if (rc) return rc;
+    if ((rc = ensure_dense(c, l))) return rc;
     int ne, nc;
     double Lam;
     cheb_defaults(o, ne, nc, Lam);
     Work<T>& W = work_of<T>(c->lv[l]);
     const long long n = c->lv[l].h.n_dofs();
     cudaStream_t st = c->st;
-    if ((rc = apply_t<T>(c, l, x, W.Ap))) return rc;
+    if ((rc = solver_apply<T>(c, l, x, W.Ap))) return rc;
     CK(residual_init<T>(b, W.Ap, W.r, W.p, n, c->red, st));
     CK(sm_init(W.sm, c->red.out, st));
     c->launches += 3;
     for (int k = 0; k < ne; ++k) {
-        if ((rc = apply_t<T>(c, l, W.p, W.Ap))) return rc;
+        if ((rc = solver_apply<T>(c, l, W.p, W.Ap))) return rc;
         CK(cg_alpha_fused<T>(W.sm, W.p, W.Ap, n, c->red, st));
         CK(cg_update_fused<T>(W.sm, x, W.r, W.p, W.Ap, n, c->red, st));
         CK(cg_p_update<T>(W.sm, W.p, W.r, n, st));
@@ -168,7 +232,7 @@ int smooth_t(dg_ctx* c, int l, const T* b, T* x, const dg_cheb_opts* o) {
     CK(cudaMemsetAsync(W.p, 0, n * sizeof(T), st));
     c->launches += 1;
     for (int k = 0; k < nc; ++k) {
-        if ((rc = apply_t<T>(c, l, x, W.Ap))) return rc;
+        if ((rc = solver_apply<T>(c, l, x, W.Ap))) return rc;
         CK(cheb_step<T>(W.sm, k, b, W.Ap, W.p, x, n, st));
         c->launches += 1;
     }
@@ -272,7 +336,7 @@ int vcycle_t(dg_ctx* c, const T* f, T* v, const dg_mg_opts* o) {
         Work<T>& W = work_of<T>(c->lv[l]);
         CK(cudaMemsetAsync(V(l), 0, n * sizeof(T), st));
         if ((rc = smooth_t<T>(c, l, F(l), V(l), co))) return rc;
-        if ((rc = apply_t<T>(c, l, V(l), W.t))) return rc;
+        if ((rc = solver_apply<T>(c, l, V(l), W.t))) return rc;
         CK(sub3<T>(F(l), W.t, W.r, n, st));
         CK(launch_restrict<T>(tview<T>(c, l - 1), W.r, work_of<T>(c->lv[l - 1]).f, st));
         c->launches += 2;
@@ -312,7 +376,8 @@ int vcycle_maybe_graph(dg_ctx* c, int prec, double* r, double* v, const dg_mg_op
         return vcycle_t<double>(c, r, v, mo);
     };
     if (graph_mode != 0 || c->st == nullptr) return eager();
-    if (c->vgraph && c->vgraph_prec == prec && c->vgraph_epoch == c->epoch && same_opts(c->vgraph_opts, mo)) {
+    if (c->vgraph && c->vgraph_prec == prec && c->vgraph_epoch == c->epoch && c->vgraph_opver == c->op_version &&
+        same_opts(c->vgraph_opts, mo)) {
         CK(cudaGraphLaunch(c->vgraph, c->st));
         c->launches += c->vgraph_launches;
         return DG_OK;
@@ -343,6 +408,7 @@ int vcycle_maybe_graph(dg_ctx* c, int prec, double* r, double* v, const dg_mg_op
     c->launches = before;   // captured, not executed
     c->vgraph_prec = prec;
     c->vgraph_epoch = c->epoch;
+    c->vgraph_opver = c->op_version;
     c->vgraph_opts = mo ? *mo : dg_mg_opts{};
     return DG_OK;
 }

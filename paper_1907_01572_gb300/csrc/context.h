@@ -63,6 +63,10 @@ struct LevelDev {
     float* Ob32 = nullptr;
     long long* Ob_off = nullptr;
     bool z_active = false;            // zeroth-order term (c0 on the finest level, Ob on coarse levels) in use
+    double* dense64 = nullptr;        // assembled operator of a small level (column-major), solver use only
+    float* dense32 = nullptr;
+    double* denseL = nullptr;         // its SIPG (Laplacian) part, built once; + Galerkin blocks -> dense64
+    long long dense_version = -1;     // op_version the dense operator was built for
     // Galerkin structure of a coarse level: finest descendants and their reference maps
     int *g_desc_off = nullptr, *g_desc = nullptr;
     double* g_map = nullptr;
@@ -105,8 +109,10 @@ struct dg_ctx {
     cudaGraphExec_t vgraph = nullptr;
     int vgraph_prec = -1;
     long long vgraph_epoch = -1;
+    long long vgraph_opver = -1;    // operator version the graph's small-level matrices belong to
     long long vgraph_launches = 0;  // kernels in the graph
     dg_mg_opts vgraph_opts{};
     long long epoch = 0;            // bumped whenever kernel arguments of the solver change
+    long long op_version = 0;       // bumped whenever operator coefficients change (zeroth-order term)
     long long launches = 0;
 };

@@ -108,6 +108,7 @@ int build_galerkin(dg_ctx* c) {
         g.chk = device_check_flag();
         CK2(launch_galerkin(g, F.c0_64, L.Ob64, L.Ob32, c->st));
         c->launches += 1;
+        ++c->op_version;
         if (!L.z_active) ++c->epoch;
         L.z_active = true;
     }
@@ -119,7 +120,10 @@ int build_galerkin(dg_ctx* c) {
 void set_zeroth_active(dg_ctx* c, bool on) {
     for (auto& L : c->lv) {
         const bool v = on && (L.c0_64 != nullptr || L.Ob64 != nullptr);
-        if (v != L.z_active) ++c->epoch;   // kernel arguments of the captured V-cycle change
+        if (v != L.z_active) {
+            ++c->epoch;        // kernel arguments of the captured V-cycle change
+            ++c->op_version;   // assembled small-level operators are stale
+        }
         L.z_active = v;
     }
 }
