@@ -5,7 +5,8 @@
 
 namespace dg {
 cudaError_t launch_apply_bf16(const LevelView<float>& L, const BucketInfo* buckets, const void* x, float* y,
-                              cudaStream_t st, int* launches) {
-    return launch_apply_x<float, __nv_bfloat16>(L, buckets, static_cast<const __nv_bfloat16*>(x), y, st, launches);
+                              cudaStream_t st, int* launches, int* plan) {
+    return launch_apply_x<float, __nv_bfloat16>(L, buckets, static_cast<const __nv_bfloat16*>(x), y, st, launches,
+                                                plan);
 }
 }  // namespace dg

@@ -53,8 +53,9 @@ __device__ inline void tangential(int d, int& t1, int& t2) {
 
 // out = M in along direction DIR of an N^3 array held by one warp (TRANS: M^T; ACC: out +=).
 template <int N, int DIR, bool TRANS, bool ACC, typename T>
-__device__ inline void wpass(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ M, int lane) {
-    for (int pid = lane; pid < N * N; pid += 32) {
+__device__ inline void wpass(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ M, int lane,
+                             int nt = 32) {
+    for (int pid = lane; pid < N * N; pid += nt) {
         int base, stride;
         if (DIR == 0) { base = pid * N; stride = 1; }
         else if (DIR == 1) { base = (pid / N) * N * N + (pid % N); stride = N; }
@@ -414,8 +415,8 @@ __global__ void element_kernel(LevelView<T> L, const int* __restrict__ bucket, i
 }
 
 // All degree buckets of a level in one launch (used on small levels, where
-// launch latency rather than bandwidth bounds the apply): CTA ranges map to
-// buckets; each CTA runs the body compiled for its bucket's degree.
+// latency rather than bandwidth bounds the apply): CTA ranges map to buckets;
+// each CTA runs the code compiled for its bucket's degree.
 struct FusedBuckets {
     int nb;
     int n[kNumN];
@@ -454,6 +455,144 @@ __global__ void element_fused(LevelView<T> L, FusedBuckets fb, const TX* __restr
     const int b = fused_bucket(fb);
     const int blk = blockIdx.x - fb.cta_start[b], nblk = fb.cta_start[b + 1] - fb.cta_start[b];
     DG_BODY_SWITCH(fb.n[b], (element_body<NN, T, TX>(L, fb.elems[b], fb.count[b], x, y, blk, nblk)))
+}
+
+
+// ---- small levels: one CTA per element ------------------------------------------
+// The warps of the CTA split the element's mortar slots (each lifts into its own
+// accumulator, summed in warp order at the end) and share the volume passes, so
+// the latency of one element -- which bounds the apply on levels with few
+// elements -- drops several-fold.
+constexpr int kCtaWarps = 8;
+
+template <int N>
+struct CtaLayout {
+    static constexpr int N3 = N * N * N;
+    static constexpr int TWARP = Layout<N>::TFACE;                  // per-warp trace scratch
+    static constexpr int TSHARED = N3;                              // U
+    static constexpr int EWARP = N3 + 4 * kQ * kQ + 3 * kQ * N;     // per-warp lift accumulator + scratch
+    static constexpr int ESHARED = 6 * N3;                          // U, Y, A, B, G1, G3
+};
+
+template <int N, typename T, typename TX>
+__device__ __forceinline__ void trace_body_cta(const LevelView<T>& L, int e, const TX* __restrict__ x,
+                                               T* __restrict__ mt) {
+    using Ly = CtaLayout<N>;
+    const T* sFT;
+    T *sI, *sDg, *sDL;
+    T* base = load_tables<N, T>(L, sFT, sI, sDg, sDL);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    T* U = base;
+    T* F = U + Ly::TSHARED + warp * Ly::TWARP;
+    const long long dofo = L.dof_off[e];
+    for (int k = threadIdx.x; k < Ly::N3; k += blockDim.x) U[k] = ld<T>(x + dofo + k);
+    __syncthreads();
+    const int s0 = L.slot_off[e], s1 = L.slot_off[e + 1];
+    for (int si = s0 + warp; si < s1; si += nw) {
+        const SlotInfo<T> s = slot_info(L, si);
+        DG_Q_SWITCH(s.q, (trace_slot<N, Q, T>(L, s, U, sDL, sFT, F, mt, lane)))
+    }
+}
+
+template <int N, typename T, typename TX>
+__device__ __forceinline__ void element_body_cta(const LevelView<T>& L, int e, const TX* __restrict__ x,
+                                                 T* __restrict__ y) {
+    using Ly = CtaLayout<N>;
+    constexpr int N3 = Ly::N3;
+    const T* sFT;
+    T *sI, *sDg, *sDL;
+    T* base = load_tables<N, T>(L, sFT, sI, sDg, sDL);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    T* U = base;
+    T* Y = U + N3;
+    T* A = Y + N3;
+    T* B = A + N3;
+    T* G1 = B + N3;
+    T* G3 = G1 + N3;
+    T* G2 = Y;
+    T* Yw = base + Ly::ESHARED + warp * Ly::EWARP;
+    T* F = Yw + N3;
+    const long long dofo = L.dof_off[e], vo = L.vqp_off[e];
+    const bool mass = L.c0 != nullptr;
+    for (int k = tid; k < N3; k += nt) U[k] = ld<T>(x + dofo + k);
+    __syncthreads();
+    wpass<N, 0, false, false>(U, A, sI, tid, nt);
+    __syncthreads();
+    wpass<N, 1, false, false>(A, B, sI, tid, nt);
+    __syncthreads();
+    wpass<N, 2, false, false>(B, A, sI, tid, nt);
+    __syncthreads();
+    wpass<N, 0, false, false>(A, G1, sDg, tid, nt);
+    wpass<N, 1, false, false>(A, G2, sDg, tid, nt);
+    wpass<N, 2, false, false>(A, G3, sDg, tid, nt);
+    __syncthreads();
+    {
+        const T* Ge = L.G + 6 * vo;
+        for (int k = tid; k < N3; k += nt) {
+            const T g0 = G1[k], g1 = G2[k], g2 = G3[k];
+            const T m00 = Ge[k], m01 = Ge[N3 + k], m02 = Ge[2 * N3 + k];
+            const T m11 = Ge[3 * N3 + k], m12 = Ge[4 * N3 + k], m22 = Ge[5 * N3 + k];
+            G1[k] = m00 * g0 + m01 * g1 + m02 * g2;
+            G2[k] = m01 * g0 + m11 * g1 + m12 * g2;
+            G3[k] = m02 * g0 + m12 * g1 + m22 * g2;
+            if (mass) B[k] = L.c0[vo + k] * A[k];
+        }
+    }
+    __syncthreads();
+    if (mass) wpass<N, 0, true, true>(G1, B, sDg, tid, nt);
+    else wpass<N, 0, true, false>(G1, B, sDg, tid, nt);
+    __syncthreads();
+    wpass<N, 1, true, true>(G2, B, sDg, tid, nt);
+    __syncthreads();
+    wpass<N, 2, true, true>(G3, B, sDg, tid, nt);
+    __syncthreads();
+    wpass<N, 0, true, false>(B, A, sI, tid, nt);
+    __syncthreads();
+    wpass<N, 1, true, false>(A, B, sI, tid, nt);
+    __syncthreads();
+    wpass<N, 2, true, false>(B, Y, sI, tid, nt);
+    __syncthreads();
+    if (L.Ob != nullptr && L.Ob_off[e] + (long long)N3 * N3 > L.ob_total) {
+        if (tid == 0) atomicExch(L.chk, 1);
+    } else if (L.Ob != nullptr) {
+        const T* Oe = L.Ob + L.Ob_off[e];
+        for (int k = tid; k < N3; k += nt) {
+            T sacc = 0;
+            for (int j = 0; j < N3; ++j) sacc += Oe[(long long)j * N3 + k] * U[j];
+            Y[k] += sacc;
+        }
+    }
+    for (int k = lane; k < N3; k += 32) Yw[k] = 0;
+    __syncwarp();
+    const int s0 = L.slot_off[e], s1 = L.slot_off[e + 1];
+    for (int si = s0 + warp; si < s1; si += nw) {
+        const int mi = L.slot_mortar[si];
+        const SlotInfo<T> s = slot_info(L, si);
+        const bool interior = L.mortars[mi].eB >= 0;
+        const T sig = L.sigma[mi];
+        DG_Q_SWITCH(s.q, (lift_slot<N, Q, T>(L, s, interior, sig, Yw, sDL, sFT, F, L.mt, lane)))
+    }
+    __syncthreads();
+    for (int k = tid; k < N3; k += nt) {
+        T acc = Y[k];
+        for (int w = 0; w < nw; ++w) acc += base[Ly::ESHARED + w * Ly::EWARP + k];
+        y[dofo + k] = acc;
+    }
+}
+
+template <typename T, typename TX>
+__global__ void trace_cta(LevelView<T> L, FusedBuckets fb, const TX* __restrict__ x, T* __restrict__ mt) {
+    const int b = fused_bucket(fb);
+    const int e = fb.elems[b][blockIdx.x - fb.cta_start[b]];
+    DG_BODY_SWITCH(fb.n[b], (trace_body_cta<NN, T, TX>(L, e, x, mt)))
+}
+
+template <typename T, typename TX>
+__global__ void element_cta(LevelView<T> L, FusedBuckets fb, const TX* __restrict__ x, T* __restrict__ y) {
+    const int b = fused_bucket(fb);
+    const int e = fb.elems[b][blockIdx.x - fb.cta_start[b]];
+    DG_BODY_SWITCH(fb.n[b], (element_body_cta<NN, T, TX>(L, e, x, y)))
 }
 
 inline int& sm_count() {
@@ -547,11 +686,12 @@ cudaError_t launch_element(const LevelView<T>& L, const BucketInfo& b, const TX*
 namespace apply_detail {
 
 constexpr int kFusedWarps = 8;
-constexpr int kFusedMaxElems = 1216;   // 152 SMs x 8 warps: levels this small use the single-launch path
+constexpr int kFusedMaxElems = 8192;   // levels this small use one launch per kernel (warp per element)
+constexpr int kCtaMaxElems = 152;      // ... and at most one element per SM: one CTA per element
 
 template <typename T, typename TX>
-cudaError_t launch_fused(const LevelView<T>& L, const BucketInfo* buckets, const TX* x, T* y, cudaStream_t st,
-                         int* launches) {
+cudaError_t launch_fused_warp(const LevelView<T>& L, const BucketInfo* buckets, const TX* x, T* y, cudaStream_t st,
+                              int* launches) {
     const size_t cap = 220 * 1024;
     const size_t table_vals_base = (sizeof(T) == 4 ? ((L.ft.total + 3) & ~3) : 0);
     size_t max_tw = 0, max_ew = 0, max_tv = 0;
@@ -598,13 +738,57 @@ cudaError_t launch_fused(const LevelView<T>& L, const BucketInfo* buckets, const
     return err;
 }
 
+template <typename T, typename TX>
+cudaError_t launch_fused_cta(const LevelView<T>& L, const BucketInfo* buckets, const TX* x, T* y, cudaStream_t st,
+                             int* launches) {
+    const size_t cap = 220 * 1024;
+    const size_t table_vals_base = (sizeof(T) == 4 ? ((L.ft.total + 3) & ~3) : 0);
+    size_t smem_t = 0, smem_e = 0;
+    FusedBuckets fb{};
+    int ctas = 0;
+    for (int n = kMinN; n <= kMaxN; ++n) {
+        const BucketInfo& b = buckets[n];
+        if (b.count == 0) continue;
+        size_t tsh = 0, tw = 0, esh = 0, ew = 0;
+        DG_N_SWITCH(n, (tsh = CtaLayout<NN>::TSHARED, tw = CtaLayout<NN>::TWARP, esh = CtaLayout<NN>::ESHARED,
+                        ew = CtaLayout<NN>::EWARP))
+        const size_t tv = table_vals_base + 3 * (size_t)n * n;
+        smem_t = std::max(smem_t, (tv + tsh + kCtaWarps * tw) * sizeof(T));
+        smem_e = std::max(smem_e, (tv + esh + kCtaWarps * ew) * sizeof(T));
+        fb.n[fb.nb] = n;
+        fb.elems[fb.nb] = b.elems;
+        fb.count[fb.nb] = b.count;
+        fb.cta_start[fb.nb] = ctas;
+        ctas += b.count;
+        ++fb.nb;
+    }
+    fb.cta_start[fb.nb] = ctas;
+    if (ctas == 0) return cudaSuccess;
+    if (smem_e > cap || smem_t > cap) return cudaErrorInvalidConfiguration;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e1 = cudaFuncSetAttribute(trace_cta<T, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+        cudaError_t e2 = cudaFuncSetAttribute(element_cta<T, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+        if (e1 != cudaSuccess) return e1;
+        if (e2 != cudaSuccess) return e2;
+        attr = true;
+    }
+    trace_cta<T, TX><<<ctas, kCtaWarps * 32, smem_t, st>>>(L, fb, x, L.mt);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    element_cta<T, TX><<<ctas, kCtaWarps * 32, smem_e, st>>>(L, fb, x, y);
+    err = cudaGetLastError();
+    if (launches) *launches += 2;
+    return err;
+}
+
 }  // namespace apply_detail
 
 template <typename T, typename TX>
-cudaError_t launch_apply_x(const LevelView<T>& L, const BucketInfo* buckets, const TX* x, T* y, cudaStream_t st,
-                           int* launches) {
-    if (L.n_elems <= apply_detail::kFusedMaxElems)
-        return apply_detail::launch_fused<T, TX>(L, buckets, x, y, st, launches);
+cudaError_t launch_path(int path, const LevelView<T>& L, const BucketInfo* buckets, const TX* x, T* y,
+                        cudaStream_t st, int* launches) {
+    if (path == 0) return apply_detail::launch_fused_cta<T, TX>(L, buckets, x, y, st, launches);
+    if (path == 1) return apply_detail::launch_fused_warp<T, TX>(L, buckets, x, y, st, launches);
     for (int n = kMinN; n <= kMaxN; ++n) {   // every element's mortar traces first ...
         const BucketInfo& b = buckets[n];
         if (b.count == 0) continue;
@@ -624,10 +808,66 @@ cudaError_t launch_apply_x(const LevelView<T>& L, const BucketInfo* buckets, con
     return cudaSuccess;
 }
 
+// Launch plan of a level: 0 one CTA per element, 1 one warp per element in a
+// single launch per kernel, 2 per-degree-bucket launches with occupancy-sized
+// CTAs.  With a plan slot and outside stream capture the first apply times
+// the three (each writes the same outputs) and keeps the fastest; otherwise a
+// size rule picks.
+template <typename T, typename TX>
+cudaError_t launch_apply_x(const LevelView<T>& L, const BucketInfo* buckets, const TX* x, T* y, cudaStream_t st,
+                           int* launches, int* plan) {
+    int path = L.n_elems <= apply_detail::kCtaMaxElems ? 0 : (L.n_elems <= apply_detail::kFusedMaxElems ? 1 : 2);
+    if (plan && *plan >= 0) return launch_path<T, TX>(*plan, L, buckets, x, y, st, launches);
+    unsigned long long key = 1469598103934665603ull;   // FNV-1a over the level shape and precision
+    auto mix = [&](unsigned long long v) { key = (key ^ v) * 1099511628211ull; };
+    mix(sizeof(T));
+    mix(sizeof(TX));
+    mix((unsigned long long)L.n_elems);
+    for (int n = kMinN; n <= kMaxN; ++n) mix((unsigned long long)buckets[n].count);
+    if (plan) {
+        const int cached = plan_cache_get(key);
+        if (cached >= 0) {
+            *plan = cached;
+            return launch_path<T, TX>(cached, L, buckets, x, y, st, launches);
+        }
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (plan && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best = 1e30f;
+        int best_path = path;
+        for (int cand = 0; cand < 3; ++cand) {
+            cudaError_t err = launch_path<T, TX>(cand, L, buckets, x, y, st, nullptr);   // warm-up / validity
+            if (err != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < 3; ++r) launch_path<T, TX>(cand, L, buckets, x, y, st, nullptr);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_path = cand;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        *plan = best_path;
+        plan_cache_put(key, best_path);
+        path = best_path;
+    }
+    return launch_path<T, TX>(path, L, buckets, x, y, st, launches);
+}
+
 template <typename T>
 cudaError_t launch_apply(const LevelView<T>& L, const BucketInfo* buckets, const T* x, T* y, cudaStream_t st,
-                         int* launches) {
-    return launch_apply_x<T, T>(L, buckets, x, y, st, launches);
+                         int* launches, int* plan) {
+    return launch_apply_x<T, T>(L, buckets, x, y, st, launches, plan);
 }
 
 }  // namespace dg

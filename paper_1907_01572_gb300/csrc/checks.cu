@@ -3,6 +3,7 @@
 // report the launch by name).
 #include <cstdlib>
 #include <mutex>
+#include <unordered_map>
 
 #include "internal.h"
 
@@ -26,6 +27,22 @@ int* device_check_flag() {
         }
     }
     return g_flag_addr[dev];
+}
+
+namespace {
+std::mutex g_plan_mu;
+std::unordered_map<unsigned long long, int> g_plans;
+}  // namespace
+
+int plan_cache_get(unsigned long long key) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto it = g_plans.find(key);
+    return it == g_plans.end() ? -1 : it->second;
+}
+
+void plan_cache_put(unsigned long long key, int plan) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    g_plans.emplace(key, plan);
 }
 
 bool debug_sync() {

@@ -113,7 +113,8 @@ Work<float>& work_of<float>(LevelDev& L) { return L.w32; }
 template <typename T>
 int apply_t(dg_ctx* c, int l, const T* x, T* y) {
     int launches = 0;
-    CK(launch_apply<T>(view<T>(c, l), c->lv[l].buckets, x, y, c->st, &launches));
+    CK(launch_apply<T>(view<T>(c, l), c->lv[l].buckets, x, y, c->st, &launches,
+                       &c->lv[l].plan[sizeof(T) == 8 ? 0 : 1]));
     c->launches += launches;
     return DG_OK;
 }
@@ -688,7 +689,8 @@ int dg_apply(dg_ctx* c, int level, int prec, const void* x, void* y) {
     if (prec == DG_FP32) return apply_t<float>(c, level, (const float*)x, (float*)y);
     if (prec == DG_BF16) {
         int launches = 0;
-        CK(launch_apply_bf16(view<float>(c, level), c->lv[level].buckets, x, (float*)y, c->st, &launches));
+        CK(launch_apply_bf16(view<float>(c, level), c->lv[level].buckets, x, (float*)y, c->st, &launches,
+                             &c->lv[level].plan[2]));
         c->launches += launches;
         return DG_OK;
     }

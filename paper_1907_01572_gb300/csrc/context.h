@@ -67,6 +67,7 @@ struct LevelDev {
     float* dense32 = nullptr;
     double* denseL = nullptr;         // its SIPG (Laplacian) part, built once; + Galerkin blocks -> dense64
     long long dense_version = -1;     // op_version the dense operator was built for
+    int plan[3] = {-1, -1, -1};       // tuned apply launch plan per precision (FP64, FP32, BF16 operands)
     // Galerkin structure of a coarse level: finest descendants and their reference maps
     int *g_desc_off = nullptr, *g_desc = nullptr;
     double* g_map = nullptr;

@@ -129,6 +129,11 @@ struct LevelView {         // passed by value to kernels
 // Self-check support: kernels that index with offsets read from tables check
 // them against the buffer sizes, skip the access and record a code here.
 int* device_check_flag();          // device pointer to one int (0 = ok)
+// Process-wide cache of tuned apply launch plans keyed by level shape and
+// precision, so every context with the same level shape uses the same plan
+// (and therefore the same summation order) within a process.
+int plan_cache_get(unsigned long long key);   // -1 if absent
+void plan_cache_put(unsigned long long key, int plan);
 bool debug_sync();                 // DGELL_DEBUG_SYNC=1: synchronise and name every checked launch
 
 struct DevBuf {

@@ -59,3 +59,35 @@ def test_sweep32_sampled_elements_fp64_fp32():
     a2 = float(torch.dot(z, y64))
     assert abs(a1 - a2) < 1e-10 * abs(a1)
     ctx.close()
+
+
+@pytest.mark.parametrize("level", [3, 4])
+def test_mid_size_levels_sampled(level):
+    """Meshes of 960 and 7,680 elements run the single-launch warp-per-element
+    path (the smallest test meshes run the CTA-per-element path and the full
+    sweep the per-bucket path): sampled elements against the oracle."""
+    import torch
+    from paper_1907_01572_gb300 import dgell
+    desc = inputs.sweep_mesh(level=level, seed=0)
+    m = oracle_mesh(desc)
+    ctx = dgell.Context(desc)
+    x = inputs.random_vector(m.n_dofs, seed=3)
+    xd = torch.tensor(x, device="cuda")
+    y = torch.empty_like(xd)
+    ctx.apply(xd, y)
+    y32 = torch.empty_like(xd.float())
+    ctx.apply(xd.float(), y32)
+    rng = np.random.default_rng(level)
+    sample = sorted(set(rng.choice(m.n_elems, 12, replace=False).tolist() + [0, m.n_elems - 1]))
+    ref = sipg.apply_local(m, x, 10.0, elems=sample)
+    ref32 = sipg.apply_local(m, xd.float().double().cpu().numpy(), 10.0, elems=sample)
+    yh, y32h = y.cpu().numpy(), y32.double().cpu().numpy()
+    num = den = num32 = den32 = 0.0
+    for e in sample:
+        a, b = m.dof_off[e], m.dof_off[e + 1]
+        num += np.sum((yh[a:b] - ref[e]) ** 2)
+        num32 += np.sum((y32h[a:b] - ref32[e]) ** 2)
+        den += np.sum(ref[e] ** 2)
+        den32 += np.sum(ref32[e] ** 2)
+    assert np.sqrt(num / den) < 1e-12 and np.sqrt(num32 / den32) < 1e-5
+    ctx.close()
