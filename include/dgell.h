@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define DGELL_VERSION 104
+#define DGELL_VERSION 105
 
 enum {
     DG_OK = 0,

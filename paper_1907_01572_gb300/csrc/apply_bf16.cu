@@ -5,8 +5,8 @@
 
 namespace dg {
 cudaError_t launch_apply_bf16(const LevelView<float>& L, const BucketInfo* buckets, const void* x, float* y,
-                              cudaStream_t st, int* launches, int* plan) {
+                              cudaStream_t st, int* launches, int* plan, const ApplyStreams* as) {
     return launch_apply_x<float, __nv_bfloat16>(L, buckets, static_cast<const __nv_bfloat16*>(x), y, st, launches,
-                                                plan);
+                                                plan, as);
 }
 }  // namespace dg

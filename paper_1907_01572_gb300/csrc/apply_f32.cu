@@ -3,5 +3,5 @@
 
 namespace dg {
 template cudaError_t launch_apply<float>(const LevelView<float>&, const BucketInfo*, const float*, float*,
-                                         cudaStream_t, int*, int*);
+                                         cudaStream_t, int*, int*, const ApplyStreams*);
 }  // namespace dg

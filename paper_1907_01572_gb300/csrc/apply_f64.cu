@@ -3,5 +3,5 @@
 
 namespace dg {
 template cudaError_t launch_apply<double>(const LevelView<double>&, const BucketInfo*, const double*, double*,
-                                          cudaStream_t, int*, int*);
+                                          cudaStream_t, int*, int*, const ApplyStreams*);
 }  // namespace dg

@@ -31,6 +31,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "apply.h"
 
@@ -49,6 +50,23 @@ __device__ __forceinline__ T ld(const TX* p) {
 __device__ inline void tangential(int d, int& t1, int& t2) {
     t1 = d == 0 ? 1 : 0;
     t2 = d == 2 ? 1 : 2;
+}
+
+// Per-warp arrays start on multiples of four values (16-byte boundaries).
+constexpr int r4(int v) { return (v + 3) & ~3; }
+
+// One (Im, Dm) pair of the mortar tables: a single 8- or 16-byte access.
+template <typename T>
+__device__ __forceinline__ void ld2(const T* p, T& a, T& b) {
+    if constexpr (sizeof(T) == 4) {
+        const float2 v = *reinterpret_cast<const float2*>(p);
+        a = v.x;
+        b = v.y;
+    } else {
+        const double2 v = *reinterpret_cast<const double2*>(p);
+        a = v.x;
+        b = v.y;
+    }
 }
 
 // out = M in along direction DIR of an N^3 array held by one warp (TRANS: M^T; ACC: out +=).
@@ -93,11 +111,12 @@ __device__ __forceinline__ SlotInfo<T> slot_info(const LevelView<T>& L, int si) 
     return s;
 }
 
-// Own trace at the Q x Q mortar points: u and dn = c^side . grad_xi u (c^side = J^-1 n_A).
+// Own trace at the Q x Q mortar points: u and dn = c^side . grad_xi u (c^side =
+// J^-1 n_A, three Q^2 blocks at co).  Mortar tables are (Im, Dm) pairs.
 template <int N, int Q, typename T>
 __device__ __forceinline__ void trace_slot(const LevelView<T>& L, const SlotInfo<T>& s, const T* __restrict__ U,
                                            const T* __restrict__ sDL, const T* __restrict__ sFT, T* F,
-                                           T* __restrict__ mt, int lane) {
+                                           const T* __restrict__ co, T* __restrict__ mt, int lane) {
     if constexpr (Q < N) {
         return;
     } else {
@@ -106,9 +125,9 @@ __device__ __forceinline__ void trace_slot(const LevelView<T>& L, const SlotInfo
         const int d = s.f >> 1, fn = (s.f & 1) ? N - 1 : 0;
         int t1, t2;
         tangential(d, t1, t2);
-        T* uf = F;
+        T* uf = F;                  // u and n . grad_xi u at the N x N face nodes
         T* df = uf + N2;
-        T* U1 = df + N2;
+        T* U1 = df + N2;            // u, d/dt1 u, dn u after the first tangential direction (Q x N)
         T* DU1 = U1 + Q * N;
         T* N1 = DU1 + Q * N;
         for (int k = lane; k < N2; k += 32) {
@@ -124,52 +143,54 @@ __device__ __forceinline__ void trace_slot(const LevelView<T>& L, const SlotInfo
             df[k] = acc;
         }
         __syncwarp();
-        const T* Im1 = sFT + L.ft.off[N - kMinN][Q - kMinN][s.p0];
-        const T* Dm1 = Im1 + Q * N;
+        const T* M1 = sFT + L.ft.off[N - kMinN][Q - kMinN][s.p0];
         for (int k = lane; k < Q * N; k += 32) {
             const int i1 = k % Q, b = k / Q;
             T su = 0, sd = 0, sn = 0;
 #pragma unroll
             for (int a = 0; a < N; ++a) {
-                const T iv = Im1[i1 * N + a], dv = Dm1[i1 * N + a];
-                const T u = uf[a + N * b];
+                T iv, dv;
+                ld2(M1 + 2 * (i1 * N + a), iv, dv);
+                const T u = uf[a + N * b], dn = df[a + N * b];
                 su += iv * u;
                 sd += dv * u;
-                sn += iv * df[a + N * b];
+                sn += iv * dn;
             }
             U1[k] = su;
             DU1[k] = sd;
             N1[k] = sn;
         }
         __syncwarp();
-        const T* Im2 = sFT + L.ft.off[N - kMinN][Q - kMinN][s.p1];
-        const T* Dm2 = Im2 + Q * N;
-        const T* mg = L.mg + 7 * s.goff + (s.side == 0 ? 1 : 4) * Q2;
+        const T* M2 = sFT + L.ft.off[N - kMinN][Q - kMinN][s.p1];
         T* out = mt + 4 * s.goff + 2 * s.side * Q2;
         for (int k = lane; k < Q2; k += 32) {
             const int i1 = k % Q, i2 = k / Q;
             T u = 0, g1 = 0, g2 = 0, gn = 0;
 #pragma unroll
             for (int b = 0; b < N; ++b) {
-                const T iv = Im2[i2 * N + b], dv = Dm2[i2 * N + b];
-                const T ub = U1[i1 + Q * b];
+                T iv, dv;
+                ld2(M2 + 2 * (i2 * N + b), iv, dv);
+                const T ub = U1[i1 + Q * b], dub = DU1[i1 + Q * b], nb = N1[i1 + Q * b];
                 u += iv * ub;
-                g1 += iv * DU1[i1 + Q * b];
+                g1 += iv * dub;
                 g2 += dv * ub;
-                gn += iv * N1[i1 + Q * b];
+                gn += iv * nb;
             }
             out[k] = u;
-            out[Q2 + k] = mg[t1 * Q2 + k] * g1 + mg[t2 * Q2 + k] * g2 + mg[d * Q2 + k] * gn;
+            out[Q2 + k] = co[t1 * Q2 + k] * g1 + co[t2 * Q2 + k] * g2 + co[d * Q2 + k] * gn;
         }
         __syncwarp();
     }
 }
 
-// Flux at the mortar points and lift into Y for one mortar of the element.
+// Flux at the mortar points and lift into Y for one mortar of the element.  Per
+// mortar point: surface weight wSp, this side's c (three Q^2 blocks at co) and
+// the trace buffer entries m = [u_A, dn_A, u_B, dn_B] (Q^2 each).
 template <int N, int Q, typename T>
 __device__ __forceinline__ void lift_slot(const LevelView<T>& L, const SlotInfo<T>& s, bool interior, T sig,
                                           T* __restrict__ Y, const T* __restrict__ sDL, const T* __restrict__ sFT,
-                                          T* F, const T* __restrict__ mt, int lane) {
+                                          T* F, const T* __restrict__ wSp, const T* __restrict__ co,
+                                          const T* __restrict__ m, int lane) {
     if constexpr (Q < N) {
         return;
     } else {
@@ -178,19 +199,16 @@ __device__ __forceinline__ void lift_slot(const LevelView<T>& L, const SlotInfo<
         const int d = s.f >> 1, fn = (s.f & 1) ? N - 1 : 0;
         int t1, t2;
         tangential(d, t1, t2);
-        T* PA = F;
+        T* PA = F;              // flux factors at the Q x Q mortar points
         T* PB1 = PA + Q2;
         T* PB2 = PB1 + Q2;
         T* PBn = PB2 + Q2;
-        T* X1 = PBn + Q2;
+        T* X1 = PBn + Q2;       // after the second tangential direction (Q x N)
         T* X2 = X1 + Q * N;
         T* X3 = X2 + Q * N;
-        const T* m = mt + 4 * s.goff;
-        const T* mg = L.mg + 7 * s.goff;
-        const T* co = mg + (s.side == 0 ? 1 : 4) * Q2;
         const T sgn = s.side == 0 ? T(1) : T(-1);
         for (int k = lane; k < Q2; k += 32) {
-            const T wS = mg[k];
+            const T wS = wSp[k];
             const T uA = m[k], dA = m[Q2 + k];
             T jmp, avg, bc;
             if (interior) {
@@ -210,14 +228,14 @@ __device__ __forceinline__ void lift_slot(const LevelView<T>& L, const SlotInfo<
             PBn[k] = b2 * co[d * Q2 + k];
         }
         __syncwarp();
-        const T* Im2 = sFT + L.ft.off[N - kMinN][Q - kMinN][s.p1];
-        const T* Dm2 = Im2 + Q * N;
+        const T* M2 = sFT + L.ft.off[N - kMinN][Q - kMinN][s.p1];
         for (int k = lane; k < Q * N; k += 32) {
             const int i1 = k % Q, b = k / Q;
             T s1v = 0, s2v = 0, s3v = 0;
 #pragma unroll
             for (int i2 = 0; i2 < Q; ++i2) {
-                const T iv = Im2[i2 * N + b], dv = Dm2[i2 * N + b];
+                T iv, dv;
+                ld2(M2 + 2 * (i2 * N + b), iv, dv);
                 s1v += iv * PA[i1 + Q * i2] + dv * PB2[i1 + Q * i2];
                 s2v += iv * PB1[i1 + Q * i2];
                 s3v += iv * PBn[i1 + Q * i2];
@@ -227,14 +245,14 @@ __device__ __forceinline__ void lift_slot(const LevelView<T>& L, const SlotInfo<
             X3[k] = s3v;
         }
         __syncwarp();
-        const T* Im1 = sFT + L.ft.off[N - kMinN][Q - kMinN][s.p0];
-        const T* Dm1 = Im1 + Q * N;
+        const T* M1 = sFT + L.ft.off[N - kMinN][Q - kMinN][s.p0];
         for (int k = lane; k < N2; k += 32) {
             const int a = k % N, b = k / N;
             T fu = 0, fd = 0;
 #pragma unroll
             for (int i1 = 0; i1 < Q; ++i1) {
-                const T iv = Im1[i1 * N + a], dv = Dm1[i1 * N + a];
+                T iv, dv;
+                ld2(M1 + 2 * (i1 * N + a), iv, dv);
                 fu += iv * X1[i1 + Q * b] + dv * X2[i1 + Q * b];
                 fd += iv * X3[i1 + Q * b];
             }
@@ -259,60 +277,136 @@ __device__ __forceinline__ void lift_slot(const LevelView<T>& L, const SlotInfo<
         default: { constexpr int Q = 9; CALL; break; }                  \
     }
 
+// Per-warp shared-memory layout (in values of T) of the warp-per-element kernels.
 template <int N>
 struct Layout {
-    static constexpr int N2 = N * N, N3 = N2 * N;
+    static constexpr int N2 = N * N, N3 = N2 * N, NR = r4(N3);
     static constexpr int TFACE = 2 * N2 + 3 * kQ * N;                 // trace kernel face scratch
-    static constexpr int TWARP = N3 + TFACE;
+    static constexpr int TWARP = NR + TFACE;
     static constexpr int EFACE = 4 * kQ * kQ + 3 * kQ * N;            // element kernel face scratch
-    static constexpr bool ALIAS = 4 * N3 >= EFACE;                    // reuses the volume scratch
-    static constexpr int EWARP = ALIAS ? 6 * N3 : 6 * N3 + EFACE;
+    static constexpr bool ALIAS = 4 * NR >= EFACE;                    // reuses the volume scratch
+    static constexpr int EWARP = ALIAS ? 6 * NR : 6 * NR + EFACE;
+};
+
+// Values ahead of the per-warp scratch: FP32 mortar tables (staged) and the
+// element's 1-D volume tables.
+template <int N>
+__host__ __device__ constexpr int table_vals(int ftot) {
+    return r4(ftot) + r4(3 * N * N);
+}
+
+// One mortar slot of an element, packed so that a warp can hold the records of
+// all of an element's slots (one per lane) and broadcast them by shuffles:
+// info = face | side << 3 | pos0 << 4 | pos1 << 6 | q << 8 | interior << 12.
+template <typename T>
+struct SlotRec {
+    int info;
+    long long goff;
+    T sig;
+};
+
+template <typename T>
+__device__ __forceinline__ SlotRec<T> load_rec(const LevelView<T>& L, int si) {
+    const int mi = L.slot_mortar[si];
+    const Mortar M = L.mortars[mi];
+    const int f = L.slot_face[si], side = L.slot_side[si];
+    const int p0 = side == 0 ? M.posA0 : M.posB0, p1 = side == 0 ? M.posA1 : M.posB1;
+    SlotRec<T> r;
+    r.info = f | side << 3 | p0 << 4 | p1 << 6 | (int)M.q << 8 | (M.eB >= 0 ? 1 << 12 : 0);
+    r.goff = M.goff;
+    r.sig = L.sigma[mi];
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ SlotInfo<T> unpack_rec(const SlotRec<T>& r) {
+    SlotInfo<T> s;
+    s.f = r.info & 7;
+    s.side = (r.info >> 3) & 1;
+    s.p0 = (r.info >> 4) & 3;
+    s.p1 = (r.info >> 6) & 3;
+    s.q = (r.info >> 8) & 15;
+    s.goff = r.goff;
+    return s;
+}
+
+// The slot records of one element, lane j holding slot s0 + j: every face is
+// covered by one or four mortars (checked when the connectivity is built), so
+// an element has 6 to 24 slots.
+template <typename T>
+struct WarpSlots {
+    int s0, s1;
+    SlotRec<T> mine;
+    __device__ __forceinline__ void load(const LevelView<T>& L, int e, int lane) {
+        s0 = L.slot_off[e];
+        s1 = L.slot_off[e + 1];
+        if (s0 + lane < s1) {
+            mine = load_rec(L, s0 + lane);
+        } else {
+            mine.info = 0;
+            mine.goff = 0;
+            mine.sig = 0;
+        }
+    }
+    __device__ __forceinline__ SlotRec<T> get(int si) const {   // warp-uniform si in [s0, s1)
+        const int src = si - s0;
+        SlotRec<T> r;
+        r.info = __shfl_sync(0xffffffffu, mine.info, src);
+        r.goff = __shfl_sync(0xffffffffu, mine.goff, src);
+        r.sig = __shfl_sync(0xffffffffu, mine.sig, src);
+        return r;
+    }
 };
 
 // Shared-memory preamble common to both kernels: mortar tables (FP32) and the
-// element's 1-D volume tables.
+// element's 1-D volume tables; returns the first per-warp scratch value.
 template <int N, typename T>
-__device__ __forceinline__ T* load_tables(const LevelView<T>& L, const T*& sFT, T*& sI, T*& sDg, T*& sDL) {
+__device__ __forceinline__ T* load_tables(const LevelView<T>& L, const T*& sFT, const T*& sI, const T*& sDg,
+                                          const T*& sDL) {
     constexpr bool STAGE = sizeof(T) == 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     const int ftot = STAGE ? L.ft.total : 0;
     T* sFTs = sm;
     sFT = STAGE ? sFTs : L.ftab;
-    sI = sFTs + ((ftot + 3) & ~3);
-    sDg = sI + N * N;
-    sDL = sDg + N * N;
+    T* sV = sFTs + r4(ftot);
     for (int k = threadIdx.x; k < ftot; k += blockDim.x) sFTs[k] = L.ftab[k];
     for (int k = threadIdx.x; k < N * N; k += blockDim.x) {
-        sI[k] = L.tab[tab_n(TabIndex::I, N) + k];
-        sDg[k] = L.tab[tab_n(TabIndex::Dg, N) + k];
-        sDL[k] = L.tab[tab_n(TabIndex::DL, N) + k];
+        sV[k] = L.tab[tab_n(TabIndex::I, N) + k];
+        sV[N * N + k] = L.tab[tab_n(TabIndex::Dg, N) + k];
+        sV[2 * N * N + k] = L.tab[tab_n(TabIndex::DL, N) + k];
     }
+    sI = sV;
+    sDg = sI + N * N;
+    sDL = sDg + N * N;
     __syncthreads();
-    return sDL + N * N;
+    return sV + r4(3 * N * N);
 }
 
+// Warp per element; every element's slot records are fetched once (a lane per
+// slot) instead of through a dependent load chain per slot.
 template <int N, typename T, typename TX>
 __device__ __forceinline__ void trace_body(const LevelView<T>& L, const int* __restrict__ bucket, int count,
                                            const TX* __restrict__ x, T* __restrict__ mt, int blk, int nblk) {
     using Ly = Layout<N>;
     constexpr int N3 = Ly::N3;
-    const T* sFT;
-    T *sI, *sDg, *sDL;
+    const T *sFT, *sI, *sDg, *sDL;
     T* wbase = load_tables<N, T>(L, sFT, sI, sDg, sDL);
     const int nwarps = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T* U = wbase + warp * Ly::TWARP;
-    T* F = U + N3;
+    T* F = U + Ly::NR;
     for (int ei = blk * nwarps + warp; ei < count; ei += nblk * nwarps) {
         const int e = bucket[ei];
         const long long dofo = L.dof_off[e];
+        WarpSlots<T> ws;
+        ws.load(L, e, lane);
         for (int k = lane; k < N3; k += 32) U[k] = ld<T>(x + dofo + k);
         __syncwarp();
-        const int s0 = L.slot_off[e], s1 = L.slot_off[e + 1];
-        for (int si = s0; si < s1; ++si) {
-            const SlotInfo<T> s = slot_info(L, si);
-            DG_Q_SWITCH(s.q, (trace_slot<N, Q, T>(L, s, U, sDL, sFT, F, mt, lane)))
+        for (int si = ws.s0; si < ws.s1; ++si) {
+            const SlotInfo<T> s = unpack_rec(ws.get(si));
+            const T* co = L.mg + 7 * s.goff + (s.side == 0 ? 1 : 4) * s.q * s.q;
+            DG_Q_SWITCH(s.q, (trace_slot<N, Q, T>(L, s, U, sDL, sFT, F, co, mt, lane)))
         }
     }
 }
@@ -327,25 +421,25 @@ template <int N, typename T, typename TX>
 __device__ __forceinline__ void element_body(const LevelView<T>& L, const int* __restrict__ bucket, int count,
                                              const TX* __restrict__ x, T* __restrict__ y, int blk, int nblk) {
     using Ly = Layout<N>;
-    constexpr int N2 = Ly::N2, N3 = Ly::N3;
-    const T* sFT;
-    T *sI, *sDg, *sDL;
+    constexpr int N3 = Ly::N3, NR = Ly::NR;
+    const T *sFT, *sI, *sDg, *sDL;
     T* wbase = load_tables<N, T>(L, sFT, sI, sDg, sDL);
     const int nwarps = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T* U = wbase + warp * Ly::EWARP;
-    T* Y = U + N3;
-    T* A = Y + N3;
-    T* B = A + N3;
-    T* G1 = B + N3;
-    T* G3 = G1 + N3;
+    T* Y = U + NR;
+    T* A = Y + NR;
+    T* B = A + NR;
+    T* G1 = B + NR;
+    T* G3 = G1 + NR;
     T* G2 = Y;  // the y-gradient lives in Y until the backward passes
-    T* F = Ly::ALIAS ? A : G3 + N3;
+    T* F = Ly::ALIAS ? A : G3 + NR;
     const bool mass = L.c0 != nullptr;
-    (void)N2;
     for (int ei = blk * nwarps + warp; ei < count; ei += nblk * nwarps) {
         const int e = bucket[ei];
         const long long dofo = L.dof_off[e], vo = L.vqp_off[e];
+        WarpSlots<T> ws;
+        ws.load(L, e, lane);
         for (int k = lane; k < N3; k += 32) U[k] = ld<T>(x + dofo + k);
         __syncwarp();
         wpass<N, 0, false, false>(U, A, sI, lane);
@@ -395,13 +489,14 @@ __device__ __forceinline__ void element_body(const LevelView<T>& L, const int* _
             }
             __syncwarp();
         }
-        const int s0 = L.slot_off[e], s1 = L.slot_off[e + 1];
-        for (int si = s0; si < s1; ++si) {
-            const int mi = L.slot_mortar[si];
-            const SlotInfo<T> s = slot_info(L, si);
-            const bool interior = L.mortars[mi].eB >= 0;
-            const T sig = L.sigma[mi];
-            DG_Q_SWITCH(s.q, (lift_slot<N, Q, T>(L, s, interior, sig, Y, sDL, sFT, F, L.mt, lane)))
+        for (int si = ws.s0; si < ws.s1; ++si) {
+            const SlotRec<T> r = ws.get(si);
+            const SlotInfo<T> s = unpack_rec(r);
+            const bool interior = (r.info >> 12) & 1;
+            const T* mg = L.mg + 7 * s.goff;
+            const T* co = mg + (s.side == 0 ? 1 : 4) * s.q * s.q;
+            DG_Q_SWITCH(s.q, (lift_slot<N, Q, T>(L, s, interior, r.sig, Y, sDL, sFT, F, mg, co, L.mt + 4 * s.goff,
+                                                 lane)))
         }
         for (int k = lane; k < N3; k += 32) y[dofo + k] = Y[k];
         __syncwarp();
@@ -467,19 +562,18 @@ constexpr int kCtaWarps = 8;
 
 template <int N>
 struct CtaLayout {
-    static constexpr int N3 = N * N * N;
-    static constexpr int TWARP = Layout<N>::TFACE;                  // per-warp trace scratch
-    static constexpr int TSHARED = N3;                              // U
-    static constexpr int EWARP = N3 + 4 * kQ * kQ + 3 * kQ * N;     // per-warp lift accumulator + scratch
-    static constexpr int ESHARED = 6 * N3;                          // U, Y, A, B, G1, G3
+    static constexpr int N3 = N * N * N, NR = r4(N3);
+    static constexpr int TWARP = Layout<N>::TFACE;                        // per-warp trace scratch
+    static constexpr int TSHARED = NR;                                    // U
+    static constexpr int EWARP = NR + 4 * kQ * kQ + 3 * kQ * N;           // per-warp lift accumulator + scratch
+    static constexpr int ESHARED = 6 * NR;                                // U, Y, A, B, G1, G3
 };
 
 template <int N, typename T, typename TX>
 __device__ __forceinline__ void trace_body_cta(const LevelView<T>& L, int e, const TX* __restrict__ x,
                                                T* __restrict__ mt) {
     using Ly = CtaLayout<N>;
-    const T* sFT;
-    T *sI, *sDg, *sDL;
+    const T *sFT, *sI, *sDg, *sDL;
     T* base = load_tables<N, T>(L, sFT, sI, sDg, sDL);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     T* U = base;
@@ -490,7 +584,8 @@ __device__ __forceinline__ void trace_body_cta(const LevelView<T>& L, int e, con
     const int s0 = L.slot_off[e], s1 = L.slot_off[e + 1];
     for (int si = s0 + warp; si < s1; si += nw) {
         const SlotInfo<T> s = slot_info(L, si);
-        DG_Q_SWITCH(s.q, (trace_slot<N, Q, T>(L, s, U, sDL, sFT, F, mt, lane)))
+        const T* co = L.mg + 7 * s.goff + (s.side == 0 ? 1 : 4) * s.q * s.q;
+        DG_Q_SWITCH(s.q, (trace_slot<N, Q, T>(L, s, U, sDL, sFT, F, co, mt, lane)))
     }
 }
 
@@ -498,21 +593,20 @@ template <int N, typename T, typename TX>
 __device__ __forceinline__ void element_body_cta(const LevelView<T>& L, int e, const TX* __restrict__ x,
                                                  T* __restrict__ y) {
     using Ly = CtaLayout<N>;
-    constexpr int N3 = Ly::N3;
-    const T* sFT;
-    T *sI, *sDg, *sDL;
+    constexpr int N3 = Ly::N3, NR = Ly::NR;
+    const T *sFT, *sI, *sDg, *sDL;
     T* base = load_tables<N, T>(L, sFT, sI, sDg, sDL);
     const int tid = threadIdx.x, nt = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
     T* U = base;
-    T* Y = U + N3;
-    T* A = Y + N3;
-    T* B = A + N3;
-    T* G1 = B + N3;
-    T* G3 = G1 + N3;
+    T* Y = U + NR;
+    T* A = Y + NR;
+    T* B = A + NR;
+    T* G1 = B + NR;
+    T* G3 = G1 + NR;
     T* G2 = Y;
     T* Yw = base + Ly::ESHARED + warp * Ly::EWARP;
-    T* F = Yw + N3;
+    T* F = Yw + NR;
     const long long dofo = L.dof_off[e], vo = L.vqp_off[e];
     const bool mass = L.c0 != nullptr;
     for (int k = tid; k < N3; k += nt) U[k] = ld<T>(x + dofo + k);
@@ -571,7 +665,9 @@ __device__ __forceinline__ void element_body_cta(const LevelView<T>& L, int e, c
         const SlotInfo<T> s = slot_info(L, si);
         const bool interior = L.mortars[mi].eB >= 0;
         const T sig = L.sigma[mi];
-        DG_Q_SWITCH(s.q, (lift_slot<N, Q, T>(L, s, interior, sig, Yw, sDL, sFT, F, L.mt, lane)))
+        const T* mg = L.mg + 7 * s.goff;
+        const T* co = mg + (s.side == 0 ? 1 : 4) * s.q * s.q;
+        DG_Q_SWITCH(s.q, (lift_slot<N, Q, T>(L, s, interior, sig, Yw, sDL, sFT, F, mg, co, L.mt + 4 * s.goff, lane)))
     }
     __syncthreads();
     for (int k = tid; k < N3; k += nt) {
@@ -643,7 +739,7 @@ cudaError_t launch_trace(const LevelView<T>& L, const BucketInfo& b, const TX* x
     static int W = 0, per_sm = 1;
     static size_t smem = 0;
     if (W == 0) {
-        const size_t table_bytes = ((sizeof(T) == 4 ? ((L.ft.total + 3) & ~3) : 0) + 3 * N * N) * sizeof(T);
+        const size_t table_bytes = table_vals<N>(sizeof(T) == 4 ? L.ft.total : 0) * sizeof(T);
         cudaError_t err = pick_warps(trace_kernel<N, T, TX>, table_bytes, Ly::TWARP * sizeof(T), W, smem, per_sm);
         if (err != cudaSuccess) return err;
     }
@@ -659,7 +755,7 @@ cudaError_t launch_element(const LevelView<T>& L, const BucketInfo& b, const TX*
     static int W = 0, per_sm = 1;
     static size_t smem = 0;
     if (W == 0) {
-        const size_t table_bytes = ((sizeof(T) == 4 ? ((L.ft.total + 3) & ~3) : 0) + 3 * N * N) * sizeof(T);
+        const size_t table_bytes = table_vals<N>(sizeof(T) == 4 ? L.ft.total : 0) * sizeof(T);
         cudaError_t err = pick_warps(element_kernel<N, T, TX>, table_bytes, Ly::EWARP * sizeof(T), W, smem, per_sm);
         if (err != cudaSuccess) return err;
     }
@@ -693,7 +789,7 @@ template <typename T, typename TX>
 cudaError_t launch_fused_warp(const LevelView<T>& L, const BucketInfo* buckets, const TX* x, T* y, cudaStream_t st,
                               int* launches) {
     const size_t cap = 220 * 1024;
-    const size_t table_vals_base = (sizeof(T) == 4 ? ((L.ft.total + 3) & ~3) : 0);
+    const int ftot = sizeof(T) == 4 ? L.ft.total : 0;
     size_t max_tw = 0, max_ew = 0, max_tv = 0;
     for (int n = kMinN; n <= kMaxN; ++n) {
         if (buckets[n].count == 0) continue;
@@ -701,7 +797,7 @@ cudaError_t launch_fused_warp(const LevelView<T>& L, const BucketInfo* buckets, 
         DG_N_SWITCH(n, (tw = Layout<NN>::TWARP, ew = Layout<NN>::EWARP))
         max_tw = std::max(max_tw, tw);
         max_ew = std::max(max_ew, ew);
-        max_tv = std::max(max_tv, table_vals_base + 3 * (size_t)n * n);
+        max_tv = std::max(max_tv, (size_t)(r4(ftot) + r4(3 * n * n)));
     }
     if (max_ew == 0) return cudaSuccess;
     int W = kFusedWarps;   // same CTA shape for every bucket; shrink until the largest degree fits
@@ -742,7 +838,7 @@ template <typename T, typename TX>
 cudaError_t launch_fused_cta(const LevelView<T>& L, const BucketInfo* buckets, const TX* x, T* y, cudaStream_t st,
                              int* launches) {
     const size_t cap = 220 * 1024;
-    const size_t table_vals_base = (sizeof(T) == 4 ? ((L.ft.total + 3) & ~3) : 0);
+    const int ftot = sizeof(T) == 4 ? L.ft.total : 0;
     size_t smem_t = 0, smem_e = 0;
     FusedBuckets fb{};
     int ctas = 0;
@@ -752,7 +848,7 @@ cudaError_t launch_fused_cta(const LevelView<T>& L, const BucketInfo* buckets, c
         size_t tsh = 0, tw = 0, esh = 0, ew = 0;
         DG_N_SWITCH(n, (tsh = CtaLayout<NN>::TSHARED, tw = CtaLayout<NN>::TWARP, esh = CtaLayout<NN>::ESHARED,
                         ew = CtaLayout<NN>::EWARP))
-        const size_t tv = table_vals_base + 3 * (size_t)n * n;
+        const size_t tv = (size_t)(r4(ftot) + r4(3 * n * n));
         smem_t = std::max(smem_t, (tv + tsh + kCtaWarps * tw) * sizeof(T));
         smem_e = std::max(smem_e, (tv + esh + kCtaWarps * ew) * sizeof(T));
         fb.n[fb.nb] = n;
@@ -786,38 +882,69 @@ cudaError_t launch_fused_cta(const LevelView<T>& L, const BucketInfo* buckets, c
 
 template <typename T, typename TX>
 cudaError_t launch_path(int path, const LevelView<T>& L, const BucketInfo* buckets, const TX* x, T* y,
-                        cudaStream_t st, int* launches) {
+                        cudaStream_t st, int* launches, const ApplyStreams* as) {
     if (path == 0) return apply_detail::launch_fused_cta<T, TX>(L, buckets, x, y, st, launches);
     if (path == 1) return apply_detail::launch_fused_warp<T, TX>(L, buckets, x, y, st, launches);
-    for (int n = kMinN; n <= kMaxN; ++n) {   // every element's mortar traces first ...
-        const BucketInfo& b = buckets[n];
-        if (b.count == 0) continue;
-        cudaError_t err = cudaSuccess;
-        DG_N_SWITCH(n, (err = apply_detail::launch_trace<NN, T, TX>(L, b, x, st)))
-        if (err != cudaSuccess) return err;
-        if (launches) ++*launches;
-    }
-    for (int n = kMinN; n <= kMaxN; ++n) {   // ... then volume + face lifts
-        const BucketInfo& b = buckets[n];
-        if (b.count == 0) continue;
-        cudaError_t err = cudaSuccess;
-        DG_N_SWITCH(n, (err = apply_detail::launch_element<NN, T, TX>(L, b, x, y, st)))
-        if (err != cudaSuccess) return err;
-        if (launches) ++*launches;
+    // Per-bucket launches, largest bucket (elements x n^3) first; plan 3 deals
+    // them round robin over the caller's stream and the side streams.
+    if (path == 2) as = nullptr;
+    int order[kNumN], nb = 0;
+    for (int n = kMinN; n <= kMaxN; ++n)
+        if (buckets[n].count > 0) order[nb++] = n;
+    auto work = [&](int n) { return (long long)buckets[n].count * n * n * n; };
+    std::sort(order, order + nb, [&](int a, int b) { return work(a) > work(b); });
+    const int ns = as ? std::min(as->n, nb - 1) : 0;
+    for (int phase = 0; phase < 2; ++phase) {   // every element's mortar traces, then volume + face lifts
+        if (ns > 0) {
+            cudaError_t err = cudaEventRecord(as->fork[phase], st);
+            for (int i = 0; i < ns && err == cudaSuccess; ++i) err = cudaStreamWaitEvent(as->side[i], as->fork[phase], 0);
+            if (err != cudaSuccess) return err;
+        }
+        for (int j = 0; j < nb; ++j) {
+            const int n = order[j], k = j % (ns + 1);
+            const cudaStream_t sj = k == 0 ? st : as->side[k - 1];
+            const BucketInfo& b = buckets[n];
+            cudaError_t err = cudaSuccess;
+            if (phase == 0) {
+                DG_N_SWITCH(n, (err = apply_detail::launch_trace<NN, T, TX>(L, b, x, sj)))
+            } else {
+                DG_N_SWITCH(n, (err = apply_detail::launch_element<NN, T, TX>(L, b, x, y, sj)))
+            }
+            if (err != cudaSuccess) return err;
+            if (launches) ++*launches;
+        }
+        for (int i = 0; i < ns; ++i) {
+            cudaError_t err = cudaEventRecord(as->join[phase][i], as->side[i]);
+            if (err == cudaSuccess) err = cudaStreamWaitEvent(st, as->join[phase][i], 0);
+            if (err != cudaSuccess) return err;
+        }
     }
     return cudaSuccess;
 }
 
 // Launch plan of a level: 0 one CTA per element, 1 one warp per element in a
 // single launch per kernel, 2 per-degree-bucket launches with occupancy-sized
-// CTAs.  With a plan slot and outside stream capture the first apply times
-// the three (each writes the same outputs) and keeps the fastest; otherwise a
-// size rule picks.
+// CTAs, 3 the same spread over side streams.  With a plan slot and outside
+// stream capture the first apply times the candidates (each writes the same
+// outputs, in the same order of summation) and keeps the fastest; otherwise a
+// size rule picks.  DGELL_APPLY_PLAN=0..3 fixes the plan of every tuned level.
+inline int forced_plan() {
+    static const int v = [] {
+        const char* e = std::getenv("DGELL_APPLY_PLAN");
+        return (e && e[0] >= '0' && e[0] <= '3' && e[1] == 0) ? e[0] - '0' : -1;
+    }();
+    return v;
+}
+
 template <typename T, typename TX>
 cudaError_t launch_apply_x(const LevelView<T>& L, const BucketInfo* buckets, const TX* x, T* y, cudaStream_t st,
-                           int* launches, int* plan) {
+                           int* launches, int* plan, const ApplyStreams* as = nullptr) {
     int path = L.n_elems <= apply_detail::kCtaMaxElems ? 0 : (L.n_elems <= apply_detail::kFusedMaxElems ? 1 : 2);
-    if (plan && *plan >= 0) return launch_path<T, TX>(*plan, L, buckets, x, y, st, launches);
+    if (plan && *plan >= 0) return launch_path<T, TX>(*plan, L, buckets, x, y, st, launches, as);
+    if (plan && forced_plan() >= 0) {
+        *plan = forced_plan();
+        return launch_path<T, TX>(*plan, L, buckets, x, y, st, launches, as);
+    }
     unsigned long long key = 1469598103934665603ull;   // FNV-1a over the level shape and precision
     auto mix = [&](unsigned long long v) { key = (key ^ v) * 1099511628211ull; };
     mix(sizeof(T));
@@ -828,7 +955,7 @@ cudaError_t launch_apply_x(const LevelView<T>& L, const BucketInfo* buckets, con
         const int cached = plan_cache_get(key);
         if (cached >= 0) {
             *plan = cached;
-            return launch_path<T, TX>(cached, L, buckets, x, y, st, launches);
+            return launch_path<T, TX>(cached, L, buckets, x, y, st, launches, as);
         }
     }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -838,14 +965,15 @@ cudaError_t launch_apply_x(const LevelView<T>& L, const BucketInfo* buckets, con
         cudaEventCreate(&e1);
         float best = 1e30f;
         int best_path = path;
-        for (int cand = 0; cand < 3; ++cand) {
-            cudaError_t err = launch_path<T, TX>(cand, L, buckets, x, y, st, nullptr);   // warm-up / validity
+        const int ncand = (as && as->n > 0) ? 4 : 3;
+        for (int cand = 0; cand < ncand; ++cand) {
+            cudaError_t err = launch_path<T, TX>(cand, L, buckets, x, y, st, nullptr, as);   // warm-up / validity
             if (err != cudaSuccess) {
                 cudaGetLastError();
                 continue;
             }
             cudaEventRecord(e0, st);
-            for (int r = 0; r < 3; ++r) launch_path<T, TX>(cand, L, buckets, x, y, st, nullptr);
+            for (int r = 0; r < 3; ++r) launch_path<T, TX>(cand, L, buckets, x, y, st, nullptr, as);
             cudaEventRecord(e1, st);
             if (cudaEventSynchronize(e1) != cudaSuccess) break;
             float ms = 0.f;
@@ -861,13 +989,13 @@ cudaError_t launch_apply_x(const LevelView<T>& L, const BucketInfo* buckets, con
         plan_cache_put(key, best_path);
         path = best_path;
     }
-    return launch_path<T, TX>(path, L, buckets, x, y, st, launches);
+    return launch_path<T, TX>(path, L, buckets, x, y, st, launches, as);
 }
 
 template <typename T>
 cudaError_t launch_apply(const LevelView<T>& L, const BucketInfo* buckets, const T* x, T* y, cudaStream_t st,
-                         int* launches, int* plan) {
-    return launch_apply_x<T, T>(L, buckets, x, y, st, launches, plan);
+                         int* launches, int* plan, const ApplyStreams* as) {
+    return launch_apply_x<T, T>(L, buckets, x, y, st, launches, plan, as);
 }
 
 }  // namespace dg

@@ -11,6 +11,38 @@
 
 using namespace dg;
 
+namespace dg {
+cudaError_t apply_streams_create(ApplyStreams& as) {
+    as.n = 0;
+    for (int i = 0; i < kApplySide; ++i) {
+        cudaError_t err = cudaStreamCreateWithFlags(&as.side[i], cudaStreamNonBlocking);
+        if (err != cudaSuccess) return err;
+        ++as.n;
+    }
+    for (int ph = 0; ph < 2; ++ph) {
+        cudaError_t err = cudaEventCreateWithFlags(&as.fork[ph], cudaEventDisableTiming);
+        for (int i = 0; i < kApplySide && err == cudaSuccess; ++i)
+            err = cudaEventCreateWithFlags(&as.join[ph][i], cudaEventDisableTiming);
+        if (err != cudaSuccess) {
+            as.n = 0;   // leave the streams unused
+            return err;
+        }
+    }
+    return cudaSuccess;
+}
+
+void apply_streams_destroy(ApplyStreams& as) {
+    for (int ph = 0; ph < 2; ++ph) {
+        if (as.fork[ph]) cudaEventDestroy(as.fork[ph]);
+        for (int i = 0; i < kApplySide; ++i)
+            if (as.join[ph][i]) cudaEventDestroy(as.join[ph][i]);
+    }
+    for (int i = 0; i < kApplySide; ++i)
+        if (as.side[i]) cudaStreamDestroy(as.side[i]);
+    as = ApplyStreams{};
+}
+}  // namespace dg
+
 namespace {
 
 thread_local std::string g_err;
@@ -110,11 +142,12 @@ Work<double>& work_of<double>(LevelDev& L) { return L.w64; }
 template <>
 Work<float>& work_of<float>(LevelDev& L) { return L.w32; }
 
+
 template <typename T>
 int apply_t(dg_ctx* c, int l, const T* x, T* y) {
     int launches = 0;
     CK(launch_apply<T>(view<T>(c, l), c->lv[l].buckets, x, y, c->st, &launches,
-                       &c->lv[l].plan[sizeof(T) == 8 ? 0 : 1]));
+                       &c->lv[l].plan[sizeof(T) == 8 ? 0 : 1], &c->as));
     c->launches += launches;
     return DG_OK;
 }
@@ -568,6 +601,7 @@ int dg_ctx_footprint(const dg_mesh_desc* mesh, const dg_disc_opts* opts, size_t*
     return DG_OK;
 }
 
+
 int dg_ctx_create(const dg_mesh_desc* mesh, const dg_disc_opts* opts, void* stream, dg_ctx** out) {
     if (!out) return fail(DG_ERR_INVALID, "out is NULL");
     *out = nullptr;
@@ -605,11 +639,19 @@ int dg_ctx_create(const dg_mesh_desc* mesh, const dg_disc_opts* opts, void* stre
         c->arena.free_all();
         return fail(DG_ERR_CUDA, "pinned host allocation failed");
     }
+    if (apply_streams_create(c->as) != cudaSuccess) {
+        cudaGetLastError();
+        apply_streams_destroy(c->as);
+        c->arena.free_all();
+        cudaFreeHost(c->red_host);
+        return fail(DG_ERR_CUDA, "stream creation failed");
+    }
     c->lv.resize(lvh.size());
     for (size_t l = 0; l < lvh.size(); ++l) c->lv[l].h = std::move(lvh[l]);
     for (size_t l = 0; l < c->lv.size(); ++l) {
         rc = upload_level(c.get(), c->lv[l], (int)l, err);
         if (rc) {
+            apply_streams_destroy(c->as);
             c->arena.free_all();
             cudaFreeHost(c->red_host);
             return fail(rc, err);
@@ -624,6 +666,7 @@ void dg_ctx_destroy(dg_ctx* c) {
     if (c->st) cudaStreamSynchronize(c->st);
     else cudaDeviceSynchronize();
     if (c->vgraph) cudaGraphExecDestroy(c->vgraph);
+    apply_streams_destroy(c->as);
     c->arena.free_all();
     if (c->red_host) cudaFreeHost(c->red_host);
     delete c;
@@ -690,7 +733,7 @@ int dg_apply(dg_ctx* c, int level, int prec, const void* x, void* y) {
     if (prec == DG_BF16) {
         int launches = 0;
         CK(launch_apply_bf16(view<float>(c, level), c->lv[level].buckets, x, (float*)y, c->st, &launches,
-                             &c->lv[level].plan[2]));
+                             &c->lv[level].plan[2], &c->as));
         c->launches += launches;
         return DG_OK;
     }

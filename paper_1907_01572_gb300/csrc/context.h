@@ -116,4 +116,5 @@ struct dg_ctx {
     long long epoch = 0;            // bumped whenever kernel arguments of the solver change
     long long op_version = 0;       // bumped whenever operator coefficients change (zeroth-order term)
     long long launches = 0;
+    dg::ApplyStreams as{};          // side streams of the per-bucket apply
 };

@@ -151,11 +151,13 @@ void build_face_tables(const std::vector<double>& tab, std::vector<double>& ftab
                     ft.off[n - kMinN][q - kMinN][pos] = -1;
                     continue;
                 }
-                ft.off[n - kMinN][q - kMinN][pos] = (int)ftab.size();
+                ft.off[n - kMinN][q - kMinN][pos] = (int)ftab.size();   // even: pairs stay aligned
                 const double* Im = &tab[tab_m(TabIndex::Im, n, q, pos)];
                 const double* Dm = &tab[tab_m(TabIndex::Dm, n, q, pos)];
-                ftab.insert(ftab.end(), Im, Im + q * n);
-                ftab.insert(ftab.end(), Dm, Dm + q * n);
+                for (int k = 0; k < q * n; ++k) {
+                    ftab.push_back(Im[k]);
+                    ftab.push_back(Dm[k]);
+                }
             }
     ft.total = (int)ftab.size();
 }

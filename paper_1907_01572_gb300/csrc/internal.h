@@ -55,7 +55,7 @@ void build_tables(std::vector<double>& tab);   // size TabIndex::Count * kTabStr
 // degree n and mortar q >= n (q = max of both sides' n), sub-face pos 0..2,
 // the q x n matrices Im then Dm, packed without padding.
 struct FaceTabs {
-    int off[kNumN][kNumN][3];   // [n-2][q-2][pos] -> offset of Im (Dm follows at + q*n); -1 if q < n
+    int off[kNumN][kNumN][3];   // [n-2][q-2][pos] -> offset of the q*n (Im, Dm) pairs (even); -1 if q < n
     int total;
 };
 void build_face_tables(const std::vector<double>& tab, std::vector<double>& ftab, FaceTabs& ft);
