@@ -23,8 +23,9 @@ sys.path.insert(0, ROOT)
 
 HBM_FALLBACK = 6800.0
 # ncu DRAM bytes (read + write) of one FP32 apply of the sweep mesh, measured for the
-# kernels of library version 104 (profiles/apply_sweep32_traffic_v4.md); null for other versions.
-TRAFFIC_BYTES_PER_APPLY = {104: 1.3634e9}
+# kernels of that library version (profiles/apply_sweep32_traffic_v4.md,
+# profiles/apply_sweep32_traffic_v105.md); null for other versions.
+TRAFFIC_BYTES_PER_APPLY = {104: 1.3634e9, 105: 1.3709e9}
 
 
 def peaks():

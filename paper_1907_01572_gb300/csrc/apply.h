@@ -14,7 +14,8 @@ struct BucketInfo {        // elements of one degree on one level
 // Side streams on which per-degree bucket kernels run next to those on the
 // caller's stream, so that one bucket's last elements overlap the next
 // bucket's first (fork and join by events; capturable into CUDA graphs).
-constexpr int kApplySide = 2;
+constexpr int kApplySide = 5;          // capacity (DGELL_APPLY_STREAMS=k, k <= 5, uses k)
+constexpr int kApplySideDefault = 1;   // two-way overlap measured fastest on the 32^3 sweep mesh
 struct ApplyStreams {
     int n = 0;                                   // side streams in use (0: the caller's stream only)
     cudaStream_t side[kApplySide] = {};

@@ -3,6 +3,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <algorithm>
+#include <cstdlib>
 #include <string>
 
 #include "context.h"
@@ -14,14 +16,16 @@ using namespace dg;
 namespace dg {
 cudaError_t apply_streams_create(ApplyStreams& as) {
     as.n = 0;
-    for (int i = 0; i < kApplySide; ++i) {
+    int want = kApplySideDefault;
+    if (const char* e = std::getenv("DGELL_APPLY_STREAMS")) want = std::max(0, std::min(kApplySide, std::atoi(e)));
+    for (int i = 0; i < want; ++i) {
         cudaError_t err = cudaStreamCreateWithFlags(&as.side[i], cudaStreamNonBlocking);
         if (err != cudaSuccess) return err;
         ++as.n;
     }
     for (int ph = 0; ph < 2; ++ph) {
         cudaError_t err = cudaEventCreateWithFlags(&as.fork[ph], cudaEventDisableTiming);
-        for (int i = 0; i < kApplySide && err == cudaSuccess; ++i)
+        for (int i = 0; i < want && err == cudaSuccess; ++i)
             err = cudaEventCreateWithFlags(&as.join[ph][i], cudaEventDisableTiming);
         if (err != cudaSuccess) {
             as.n = 0;   // leave the streams unused
