@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define DGELL_VERSION 105
+#define DGELL_VERSION 106
 
 enum {
     DG_OK = 0,

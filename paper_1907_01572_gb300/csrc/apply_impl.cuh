@@ -26,7 +26,10 @@
 // Execution: one warp per element (lanes own pencils / face points, __syncwarp
 // between phases); persistent CTAs stride over the bucket, sized for the most
 // resident warps that shared memory and registers allow; face loops are
-// compiled per mortar size q; FP32 stages every mortar table in shared memory.
+// compiled per mortar size q; FP32 stages every mortar table in shared memory
+// as (Im, Dm) pairs.  An element's mortar records are fetched once (a lane per
+// slot) and its metric terms and per-mortar data are prefetched into L2 while
+// the volume passes run, so the face stages mostly hit L2 instead of DRAM.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -69,26 +72,77 @@ __device__ __forceinline__ void ld2(const T* p, T& a, T& b) {
     }
 }
 
-// out = M in along direction DIR of an N^3 array held by one warp (TRANS: M^T; ACC: out +=).
-template <int N, int DIR, bool TRANS, bool ACC, typename T>
-__device__ inline void wpass(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ M, int lane,
-                             int nt = 32) {
-    for (int pid = lane; pid < N * N; pid += nt) {
-        int base, stride;
-        if (DIR == 0) { base = pid * N; stride = 1; }
-        else if (DIR == 1) { base = (pid / N) * N * N + (pid % N); stride = N; }
-        else { base = pid; stride = N * N; }
-        T v[N];
+// Values of the element's 1-D volume tables in shared memory: I and Dg, each
+// followed by its transpose, rows padded to a multiple of four values (a row is
+// read with 16-byte accesses, the same address in every lane), then DL (N x N).
+__host__ __device__ constexpr int vol_vals(int n) { return 4 * n * r4(n) + r4(n * n); }
+
+template <int N, typename T>
+__device__ __forceinline__ void load_row(const T* __restrict__ r, T (&m)[N]) {
+    if constexpr (sizeof(T) == 4) {
 #pragma unroll
-        for (int m = 0; m < N; ++m) v[m] = in[base + m * stride];
+        for (int j = 0; j < (N + 3) / 4; ++j) {
+            const float4 v = reinterpret_cast<const float4*>(r)[j];
+            if (4 * j < N) m[4 * j] = v.x;
+            if (4 * j + 1 < N) m[4 * j + 1] = v.y;
+            if (4 * j + 2 < N) m[4 * j + 2] = v.z;
+            if (4 * j + 3 < N) m[4 * j + 3] = v.w;
+        }
+    } else {
 #pragma unroll
-        for (int i = 0; i < N; ++i) {
+        for (int j = 0; j < (N + 1) / 2; ++j) {
+            const double2 v = reinterpret_cast<const double2*>(r)[j];
+            m[2 * j] = v.x;
+            if (2 * j + 1 < N) m[2 * j + 1] = v.y;
+        }
+    }
+}
+
+// P pencils per thread (pencil t + j nt): every row of the operator is read
+// once and applied to all of them.
+template <int N, int DIR, bool ACC, int P, typename T>
+__device__ __forceinline__ void pass_rows(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ R,
+                                          int t, int nt) {
+    constexpr int NP = r4(N);
+    constexpr int stride = DIR == 0 ? 1 : (DIR == 1 ? N : N * N);
+    T v[P][N];
+    int base[P];
+    bool ok[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        const int pid = t + j * nt;
+        ok[j] = pid < N * N;
+        base[j] = DIR == 0 ? pid * N : (DIR == 1 ? (pid / N) * N * N + (pid % N) : pid);
+#pragma unroll
+        for (int m = 0; m < N; ++m) v[j][m] = ok[j] ? in[base[j] + m * stride] : T(0);
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        T r[N];
+        load_row<N>(R + i * NP, r);
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
             T s = 0;
 #pragma unroll
-            for (int m = 0; m < N; ++m) s += (TRANS ? M[m * N + i] : M[i * N + m]) * v[m];
-            if (ACC) out[base + i * stride] += s;
-            else out[base + i * stride] = s;
+            for (int m = 0; m < N; ++m) s += r[m] * v[j][m];
+            if (ok[j]) {
+                if (ACC) out[base[j] + i * stride] += s;
+                else out[base[j] + i * stride] = s;
+            }
         }
+    }
+}
+
+// out = M in along direction DIR of an N^3 array held by nt threads (TRANS: M^T; ACC: out +=);
+// M points at the padded rows of the operator, its transpose follows.
+template <int N, int DIR, bool TRANS, bool ACC, typename T>
+__device__ inline void wpass(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ M, int t,
+                             int nt = 32) {
+    const T* R = TRANS ? M + N * r4(N) : M;
+    if (nt == 32) {
+        pass_rows<N, DIR, ACC, (N * N + 31) / 32>(in, out, R, t, 32);
+    } else {
+        for (int t0 = t; t0 < N * N; t0 += nt) pass_rows<N, DIR, ACC, 1>(in, out, R, t0, nt);
     }
 }
 
@@ -292,7 +346,7 @@ struct Layout {
 // element's 1-D volume tables.
 template <int N>
 __host__ __device__ constexpr int table_vals(int ftot) {
-    return r4(ftot) + r4(3 * N * N);
+    return r4(ftot) + vol_vals(N);
 }
 
 // One mortar slot of an element, packed so that a warp can hold the records of
@@ -330,6 +384,17 @@ __device__ __forceinline__ SlotInfo<T> unpack_rec(const SlotRec<T>& r) {
     return s;
 }
 
+// L2 prefetch of the 128-byte lines holding [p, p + n): lanes lane0, lane0 +
+// step, ... take one line each; every address issued lies inside the range.
+template <typename T>
+__device__ __forceinline__ void prefetch_l2(const T* p, long long n, int lane0, int step) {
+    const unsigned long long a0 = (unsigned long long)__cvta_generic_to_global(p), a1 = a0 + n * sizeof(T);
+    for (unsigned long long l = (a0 & ~127ull) + 128ull * lane0; l < a1; l += 128ull * step) {
+        const unsigned long long a = l < a0 ? a0 : l;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+    }
+}
+
 // The slot records of one element, lane j holding slot s0 + j: every face is
 // covered by one or four mortars (checked when the connectivity is built), so
 // an element has 6 to 24 slots.
@@ -347,6 +412,16 @@ struct WarpSlots {
             mine.goff = 0;
             mine.sig = 0;
         }
+    }
+    // This lane's slot data into L2 ahead of its use: wS and this side's c, and
+    // (lift) the mortar's trace buffer entries.
+    __device__ __forceinline__ void prefetch(const LevelView<T>& L, int lane, bool lift) const {
+        if (s0 + lane >= s1) return;
+        const int q2 = ((mine.info >> 8) & 15) * ((mine.info >> 8) & 15), side = (mine.info >> 3) & 1;
+        const T* mg = L.mg + 7 * mine.goff;
+        if (lift) prefetch_l2(mg, q2, 0, 1);
+        prefetch_l2(mg + (side ? 4 : 1) * q2, 3 * q2, 0, 1);
+        if (lift) prefetch_l2(L.mt + 4 * mine.goff, ((mine.info >> 12) & 1) ? 4 * q2 : 2 * q2, 0, 1);
     }
     __device__ __forceinline__ SlotRec<T> get(int si) const {   // warp-uniform si in [s0, s1)
         const int src = si - s0;
@@ -371,16 +446,23 @@ __device__ __forceinline__ T* load_tables(const LevelView<T>& L, const T*& sFT, 
     sFT = STAGE ? sFTs : L.ftab;
     T* sV = sFTs + r4(ftot);
     for (int k = threadIdx.x; k < ftot; k += blockDim.x) sFTs[k] = L.ftab[k];
-    for (int k = threadIdx.x; k < N * N; k += blockDim.x) {
-        sV[k] = L.tab[tab_n(TabIndex::I, N) + k];
-        sV[N * N + k] = L.tab[tab_n(TabIndex::Dg, N) + k];
-        sV[2 * N * N + k] = L.tab[tab_n(TabIndex::DL, N) + k];
+    constexpr int NP = r4(N);
+    const T* tI = L.tab + tab_n(TabIndex::I, N);
+    const T* tD = L.tab + tab_n(TabIndex::Dg, N);
+    for (int k = threadIdx.x; k < N * NP; k += blockDim.x) {
+        const int i = k / NP, m = k % NP;
+        const bool in = m < N;
+        sV[k] = in ? tI[i * N + m] : T(0);
+        sV[N * NP + k] = in ? tI[m * N + i] : T(0);
+        sV[2 * N * NP + k] = in ? tD[i * N + m] : T(0);
+        sV[3 * N * NP + k] = in ? tD[m * N + i] : T(0);
     }
+    for (int k = threadIdx.x; k < N * N; k += blockDim.x) sV[4 * N * NP + k] = L.tab[tab_n(TabIndex::DL, N) + k];
     sI = sV;
-    sDg = sI + N * N;
-    sDL = sDg + N * N;
+    sDg = sV + 2 * N * NP;
+    sDL = sV + 4 * N * NP;
     __syncthreads();
-    return sV + r4(3 * N * N);
+    return sV + vol_vals(N);
 }
 
 // Warp per element; every element's slot records are fetched once (a lane per
@@ -403,6 +485,7 @@ __device__ __forceinline__ void trace_body(const LevelView<T>& L, const int* __r
         ws.load(L, e, lane);
         for (int k = lane; k < N3; k += 32) U[k] = ld<T>(x + dofo + k);
         __syncwarp();
+        ws.prefetch(L, lane, false);   // the mortars' c, into L2 ahead of the later slots
         for (int si = ws.s0; si < ws.s1; ++si) {
             const SlotInfo<T> s = unpack_rec(ws.get(si));
             const T* co = L.mg + 7 * s.goff + (s.side == 0 ? 1 : 4) * s.q * s.q;
@@ -441,12 +524,14 @@ __device__ __forceinline__ void element_body(const LevelView<T>& L, const int* _
         WarpSlots<T> ws;
         ws.load(L, e, lane);
         for (int k = lane; k < N3; k += 32) U[k] = ld<T>(x + dofo + k);
+        prefetch_l2(L.G + 6 * vo, 6 * N3, lane, 32);   // metric terms, needed after 6 passes
         __syncwarp();
         wpass<N, 0, false, false>(U, A, sI, lane);
         __syncwarp();
         wpass<N, 1, false, false>(A, B, sI, lane);
         __syncwarp();
         wpass<N, 2, false, false>(B, A, sI, lane);  // A = u at GL points
+        ws.prefetch(L, lane, true);   // mortar data, needed after the volume terms
         __syncwarp();
         wpass<N, 0, false, false>(A, G1, sDg, lane);
         wpass<N, 1, false, false>(A, G2, sDg, lane);
@@ -797,7 +882,7 @@ cudaError_t launch_fused_warp(const LevelView<T>& L, const BucketInfo* buckets, 
         DG_N_SWITCH(n, (tw = Layout<NN>::TWARP, ew = Layout<NN>::EWARP))
         max_tw = std::max(max_tw, tw);
         max_ew = std::max(max_ew, ew);
-        max_tv = std::max(max_tv, (size_t)(r4(ftot) + r4(3 * n * n)));
+        max_tv = std::max(max_tv, (size_t)(r4(ftot) + vol_vals(n)));
     }
     if (max_ew == 0) return cudaSuccess;
     int W = kFusedWarps;   // same CTA shape for every bucket; shrink until the largest degree fits
@@ -848,7 +933,7 @@ cudaError_t launch_fused_cta(const LevelView<T>& L, const BucketInfo* buckets, c
         size_t tsh = 0, tw = 0, esh = 0, ew = 0;
         DG_N_SWITCH(n, (tsh = CtaLayout<NN>::TSHARED, tw = CtaLayout<NN>::TWARP, esh = CtaLayout<NN>::ESHARED,
                         ew = CtaLayout<NN>::EWARP))
-        const size_t tv = (size_t)(r4(ftot) + r4(3 * n * n));
+        const size_t tv = (size_t)(r4(ftot) + vol_vals(n));
         smem_t = std::max(smem_t, (tv + tsh + kCtaWarps * tw) * sizeof(T));
         smem_e = std::max(smem_e, (tv + esh + kCtaWarps * ew) * sizeof(T));
         fb.n[fb.nb] = n;
