@@ -24,8 +24,8 @@ sys.path.insert(0, ROOT)
 HBM_FALLBACK = 6800.0
 # ncu DRAM bytes (read + write) of one FP32 apply of the sweep mesh, measured for the
 # kernels of that library version (profiles/apply_sweep32_traffic_v4.md,
-# profiles/apply_sweep32_traffic_v105.md); null for other versions.
-TRAFFIC_BYTES_PER_APPLY = {104: 1.3634e9, 105: 1.3709e9}
+# profiles/apply_sweep32_traffic_v105.md, profiles/apply_sweep32_traffic_v106.md); null for other versions.
+TRAFFIC_BYTES_PER_APPLY = {104: 1.3634e9, 105: 1.3709e9, 106: 1.3770e9}
 
 
 def peaks():
@@ -38,7 +38,8 @@ def peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    """nvidia-smi sampling (every 50 ms) of SM clocks and throttle reasons; summary() keeps the
+    samples taken between mark(True) and mark(False), i.e. during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -46,26 +47,42 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.samples = []        # (host time, line)
+        self.window = [None, None]
+
+    def _reader(self):
+        for line in self.proc.stdout:
+            if line.strip():
+                self.samples.append((time.perf_counter(), line))
 
     def __enter__(self):
+        import threading
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._reader, daemon=True).start()
+            t0 = time.perf_counter()
+            while not self.samples and time.perf_counter() - t0 < 10:   # sampler running before timing
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
 
+    def mark(self, start):
+        self.window[0 if start else 1] = time.perf_counter()
+
     def __exit__(self, *a):
-        self.lines = []
         if self.proc is not None:
+            time.sleep(0.06)
             self.proc.terminate()
             try:
-                out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
-                out = ""
-            self.lines = [l for l in out.splitlines() if l.strip()]
+        t0, t1 = self.window
+        inside = [l for t, l in self.samples if t0 is not None and t1 is not None and t0 <= t <= t1 + 0.05]
+        self.lines = inside or [l for t, l in self.samples][-1:]
 
     def summary(self):
         sm, smax, reasons = [], None, set()
@@ -164,7 +181,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--level", type=int, default=5)
@@ -208,7 +225,7 @@ def main():
     y32 = torch.empty_like(x32)
     y64 = torch.empty_like(x64)
 
-    def timed(fn, steps, warmup):
+    def timed(fn, steps, warmup, clk=None):
         for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
@@ -217,11 +234,15 @@ def main():
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        if clk:
+            clk.mark(True)
         e0.record(stream)
         for _ in range(steps):
             fn()
         e1.record(stream)
         torch.cuda.synchronize()
+        if clk:
+            clk.mark(False)
         if dist:
             dist.barrier()
         return e0.elapsed_time(e1) / steps  # ms per step
@@ -229,7 +250,7 @@ def main():
     hbm, peak_kind = peaks()
     launches0 = ctx.launch_count()
     with Clocks(local) as clk:
-        ms32 = timed(lambda: ctx.apply(x32, y32), args.steps, args.warmup)
+        ms32 = timed(lambda: ctx.apply(x32, y32), args.steps, args.warmup, clk)
     launches = (ctx.launch_count() - launches0) * args.steps // (args.steps + args.warmup)
     ms64 = timed(lambda: ctx.apply(x64, y64), max(3, args.steps // 4), args.warmup)
     x16 = x64.bfloat16()
