@@ -11,6 +11,7 @@ Modules
 -------
 tables     1-D Legendre-Gauss-Lobatto / Gauss-Legendre rules, Lagrange basis (Sec. II.A.3, II.A.5)
 mesh       single-block octree mesh, element maps, mortars (Sec. II.A.1)
+blockmesh  multi-block meshes (hexahedral, cubed-sphere wedge and shell blocks), mortars across blocks
 sipg       SIPG bilinear form and right-hand side by dense quadrature (Eqs. lh2, equationFh2)
 multigrid  level meshes, prolongation, Chebyshev + CG-eigenvalue smoother, V-cycle (Sec. II.E, Algs. 3-5)
 krylov     flexible CG (Alg. 2)

@@ -178,6 +178,12 @@ class Mesh:
             if m.eB is not None:
                 self.elem_mortars[m.eB][m.fB].append(mi)
 
+    def side_ref_points(self, m, side, s1, s2):
+        """Reference coordinates on mortar m's side (0 = A, 1 = B) of its points (s1, s2)."""
+        if side == 0:
+            return self.face_ref_points(m.fA, m.posA, s1, s2)
+        return self.face_ref_points(m.fB, m.posB, s1, s2)
+
     def face_ref_points(self, f, pos, s1, s2):
         """Reference coordinates on face f of mortar points (s1, s2) for sub-face pos."""
         d, s = divmod(f, 2)

@@ -87,7 +87,7 @@ class MortarData:
         for k, (e, f, pos) in enumerate(sides):
             n = int(mesh.n[e])
             xl, _ = tables.lgl_nodes_weights(n)
-            xi = mesh.face_ref_points(f, pos, s1, s2)
+            xi = mesh.side_ref_points(m, k, s1, s2)
             J = mesh.jacobian_at(e, xi)
             detJ = np.linalg.det(J)
             Jinv = np.linalg.inv(J)
