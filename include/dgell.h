@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define DGELL_VERSION 106
+#define DGELL_VERSION 107
 
 enum {
     DG_OK = 0,
@@ -57,11 +57,39 @@ typedef enum {
     DG_MAP_SINE_WARP = 1    /* x_i += a sin(2 pi k_i x_i) sin(2 pi k_{i+1} x_{i+1}), cyclic i */
 } dg_map_kind;
 
-/* Mesh description (Sec. II.A.1: one macro-element, the box [lo, hi]^3,
- * refined as an octree).  All arrays are HOST memory; dg_ctx_create copies
- * them.  leaves: n_elems x 4 ints (level, ix, iy, iz), a level-l leaf has
- * width (hi - lo) / 2^l; leaves must tile the box with at most 2:1 level
- * difference across faces.  p: n_elems degrees in 1..8.  Geometry is
+typedef enum {
+    DG_BLOCK_HEX8 = 0,      /* trilinear map through 8 corners (a box or any parallelepiped) */
+    DG_BLOCK_WEDGE = 1,     /* cubed-sphere block between the cube of half-width a and the sphere r */
+    DG_BLOCK_SHELL = 2      /* cubed-sphere block of the shell r1 < r < r2, 1/r linear in xi_2 */
+} dg_block_kind;
+
+/* One macro-element of a multi-block mesh (Sec. II.A.1; the cubed-sphere
+ * domains of Sec. III).  Its map takes the reference cube [-1, 1]^3 to:
+ *  HEX8:  sum over corners c = i + 2 j + 4 k of corners[c] times the
+ *         trilinear weight of (i, j, k) in {0, 1}^3;
+ *  WEDGE: (1 - t) P + t r P / |P|, P = a (s e_d + xi_0 e_t1 + xi_1 e_t2),
+ *         t = (xi_2 + 1) / 2, for cube face `face` = 2 d + (s > 0);
+ *  SHELL: R(t) P / |P| with 1 / R(t) = (1 - t) / r1 + t / r2.
+ * Wedge and shell frames: (t1, t2) = (d+1, d+2) mod 3 for s = +1 and
+ * (d+2, d+1) mod 3 for s = -1, so xi_2 points outward and the frame is
+ * right-handed.  Blocks meet face to face in any relative orientation; the
+ * library finds the block connectivity by matching block face corners. */
+typedef struct {
+    int kind;              /* dg_block_kind */
+    int face;              /* WEDGE, SHELL: cube face 2 d + (s > 0) */
+    double corners[8][3];  /* HEX8 */
+    double a, r;           /* WEDGE: cube half-width, sphere radius */
+    double r1, r2;         /* SHELL: inner and outer radius */
+} dg_block;
+
+/* Mesh description (Sec. II.A.1).  With n_blocks = 0: one macro-element, the
+ * box [lo, hi]^3 (map_kind, warp_*), refined as an octree.  With n_blocks > 0:
+ * the blocks above, element e in block elem_block[e] (lo, hi and map_kind are
+ * ignored).  All arrays are HOST memory; dg_ctx_create copies them.  leaves:
+ * n_elems x 4 ints (level, ix, iy, iz) in the element's block frame (level
+ * <= 15), a level-l leaf covers 1 / 2^l of its block along each axis; leaves
+ * must tile every block with at most 2:1 level difference across faces,
+ * block interfaces included.  p: n_elems degrees in 1..8.  Geometry is
  * isoparametric: the block map is sampled at each element's own LGL nodes. */
 typedef struct {
     double lo[3];
@@ -72,6 +100,9 @@ typedef struct {
     int n_elems;
     const int* leaves;     /* host, n_elems * 4 */
     const int* p;          /* host, n_elems */
+    int n_blocks;          /* 0: single box */
+    const dg_block* blocks;    /* host, n_blocks */
+    const int* elem_block;     /* host, n_elems */
 } dg_mesh_desc;
 
 /* Discretisation options.  penalty_c is C of eq. (penaltyparameter),
@@ -118,6 +149,10 @@ int dg_level_info_get(dg_ctx* ctx, int level, dg_level_info* info);
  * element DOF offsets (n_elems + 1).  Any pointer may be NULL. */
 int dg_level_leaves(dg_ctx* ctx, int level, int* leaves, int* p, int64_t* dof_off);
 
+/* Host copy of a level's element block indices (n_elems; all 0 for a
+ * single-box mesh). */
+int dg_level_blocks(dg_ctx* ctx, int level, int* elem_block);
+
 /* Physical coordinates (device, double, 3 x n) of the level's volume GL
  * points (SoA: x[0..n), y[n..2n), z[2n..3n)), element by element, point
  * (i, j, k) of element e at vol_qp_off[e] + i + q j + q^2 k, q = p_e + 1.
@@ -152,6 +187,9 @@ typedef struct {
     int n_eigs;        /* N_iter,eigs; <= 0 -> 15 */
     int n_cheb;        /* N_iter,Cheb; <= 0 -> 15 */
     double Lambda;     /* lambda_max / lambda_min; <= 0 -> 20 */
+    double lam_scale;  /* the Chebyshev interval uses lam_scale x the CG estimate of lambda_max
+                          (a safety factor against an underestimate on strongly stretched
+                          meshes); <= 0 -> 1, the paper's Alg. 4 */
 } dg_cheb_opts;
 
 int dg_smooth(dg_ctx* ctx, int level, int prec, const void* b, void* x,

@@ -21,6 +21,13 @@ Wedge and shell frames: for cube face (axis d, sign sg) the reference axes
 0, 1, 2 point along e_{t1}, e_{t2} and outward, with (t1, t2) = (d+1, d+2)
 (mod 3) for sg = +1 and (d+2, d+1) for sg = -1 (right-handed frames).
 
+Element geometry on block meshes is exact: x and J = dx/dxi come from the
+block map itself composed with the element's linear map into its block
+(Sec. II.A.5, the Jacobian of the mapping phi_e), so shell blocks reaching
+r2 >> r1 keep a positive Jacobian at any degree and block interfaces are
+watertight.  The block-map Jacobians here are derived symbolically (sympy)
+from the formulas above.
+
 How neighbours across block boundaries are found (independent of the
 library's block connectivity and orientation codes): faces are matched by
 the physical positions of their centres and corners under the exact block
@@ -82,6 +89,70 @@ def block_map(block, xi):
     raise ValueError("unknown block kind " + str(kind))
 
 
+_JAC = {}
+
+
+def _jacobian_fn(kind, face):
+    """numpy function (xi0, xi1, xi2, params...) -> 3 x 3 entries of d x / d xi, from sympy."""
+    key = (kind, face)
+    if key in _JAC:
+        return _JAC[key]
+    import sympy
+    xi = sympy.symbols("xi0 xi1 xi2", real=True)
+    if kind == "hex8":
+        C = sympy.symbols("c0:24", real=True)
+        x = [0, 0, 0]
+        for c in range(8):
+            w = 1
+            for k in range(3):
+                w = w * ((1 + xi[k]) / 2 if (c >> k) & 1 else (1 - xi[k]) / 2)
+            for i in range(3):
+                x[i] = x[i] + w * C[3 * c + i]
+        params = C
+    else:
+        d, sg, t1, t2 = wedge_axes(face)
+        v = [0, 0, 0]
+        v[d] = sympy.Integer(int(sg))
+        v[t1] = xi[0]
+        v[t2] = xi[1]
+        length = sympy.sqrt(v[0] ** 2 + v[1] ** 2 + v[2] ** 2)
+        t = (xi[2] + 1) / 2
+        if kind == "wedge":
+            a, r = sympy.symbols("a r", positive=True)
+            x = [(1 - t) * a * v[i] + t * r * v[i] / length for i in range(3)]
+            params = (a, r)
+        else:
+            r1, r2 = sympy.symbols("r1 r2", positive=True)
+            R = 1 / ((1 - t) / r1 + t / r2)
+            x = [R * v[i] / length for i in range(3)]
+            params = (r1, r2)
+    J = [[sympy.diff(x[i], xi[l]) for l in range(3)] for i in range(3)]
+    fn = sympy.lambdify(tuple(xi) + tuple(params), J, "numpy")
+    _JAC[key] = fn
+    return fn
+
+
+def block_jacobian(block, xi):
+    """d x / d xi of the block map at reference points xi (P, 3): (P, 3, 3)."""
+    xi = np.atleast_2d(np.asarray(xi, dtype=np.float64))
+    kind = block["kind"]
+    if kind == "hex8":
+        params = np.asarray(block["corners"], dtype=np.float64).reshape(24)
+        fn = _jacobian_fn("hex8", None)
+    elif kind == "wedge":
+        params = (float(block["a"]), float(block["r"]))
+        fn = _jacobian_fn("wedge", int(block["face"]))
+    else:
+        params = (float(block["r1"]), float(block["r2"]))
+        fn = _jacobian_fn("shell", int(block["face"]))
+    J = np.zeros((len(xi), 3, 3))
+    vals = fn(xi[:, 0], xi[:, 1], xi[:, 2], *params)
+    for i in range(3):
+        for l in range(3):
+            J[:, i, l] = np.broadcast_to(np.asarray(vals[i][l], dtype=np.float64), (len(xi),))
+    return J
+
+
 class BlockMortar(Mortar):
     __slots__ = ("mapB",)
 
@@ -126,6 +197,14 @@ class BlockMesh(Mesh):
         n = int(self.n[e])
         xl, _ = tables.lgl_nodes_weights(n)
         return self.exact_point(e, tables.tensor_points(xl))
+
+    def position_at(self, e, xi):
+        return self.exact_point(e, xi)
+
+    def jacobian_at(self, e, xi):
+        """J[p, i, l] = d x_i / d xi_l of phi_e: the block map's Jacobian times 2^-level."""
+        L = int(self.leaves[e][0])
+        return block_jacobian(self.blocks[int(self.elem_block[e])], self.block_ref(e, xi)) / (2.0 ** L)
 
     def face_point_ref(self, f, b1, b2):
         d, s = divmod(f, 2)

@@ -149,8 +149,18 @@ __device__ inline void wpass(const T* __restrict__ in, T* __restrict__ out, cons
 template <typename T>
 struct SlotInfo {
     int f, side, p0, p1, q;
+    int o;                 // side B across a block interface: orientation of its face frame (blocks.h)
     long long goff;
 };
+
+// Index, in the mortar's point order (side A's face frame), of the point at
+// (j1, j2) of this side's own Q x Q face grid; the GL points are symmetric, so
+// a mirrored axis maps j to Q - 1 - j.
+template <int Q>
+__device__ __forceinline__ int mortar_index(int o, int j1, int j2) {
+    const int w1 = (o & 2) ? Q - 1 - j1 : j1, w2 = (o & 4) ? Q - 1 - j2 : j2;
+    return (o & 1) ? w2 + Q * w1 : w1 + Q * w2;
+}
 
 template <typename T>
 __device__ __forceinline__ SlotInfo<T> slot_info(const LevelView<T>& L, int si) {
@@ -161,12 +171,15 @@ __device__ __forceinline__ SlotInfo<T> slot_info(const LevelView<T>& L, int si) 
     s.p0 = s.side == 0 ? M.posA0 : M.posB0;
     s.p1 = s.side == 0 ? M.posA1 : M.posB1;
     s.q = M.q;
+    s.o = s.side == 0 ? 0 : M.orient;
     s.goff = M.goff;
     return s;
 }
 
 // Own trace at the Q x Q mortar points: u and dn = c^side . grad_xi u (c^side =
-// J^-1 n_A, three Q^2 blocks at co).  Mortar tables are (Im, Dm) pairs.
+// J^-1 n_A, three Q^2 blocks at co).  Mortar tables are (Im, Dm) pairs.  The
+// side works on its own face grid; per-point data and the trace buffer are in
+// the mortar's point order (side A's frame), reached through mortar_index.
 template <int N, int Q, typename T>
 __device__ __forceinline__ void trace_slot(const LevelView<T>& L, const SlotInfo<T>& s, const T* __restrict__ U,
                                            const T* __restrict__ sDL, const T* __restrict__ sFT, T* F,
@@ -218,7 +231,7 @@ __device__ __forceinline__ void trace_slot(const LevelView<T>& L, const SlotInfo
         const T* M2 = sFT + L.ft.off[N - kMinN][Q - kMinN][s.p1];
         T* out = mt + 4 * s.goff + 2 * s.side * Q2;
         for (int k = lane; k < Q2; k += 32) {
-            const int i1 = k % Q, i2 = k / Q;
+            const int i1 = k % Q, i2 = k / Q, kA = mortar_index<Q>(s.o, i1, i2);
             T u = 0, g1 = 0, g2 = 0, gn = 0;
 #pragma unroll
             for (int b = 0; b < N; ++b) {
@@ -230,8 +243,8 @@ __device__ __forceinline__ void trace_slot(const LevelView<T>& L, const SlotInfo
                 g2 += dv * ub;
                 gn += iv * nb;
             }
-            out[k] = u;
-            out[Q2 + k] = co[t1 * Q2 + k] * g1 + co[t2 * Q2 + k] * g2 + co[d * Q2 + k] * gn;
+            out[kA] = u;
+            out[Q2 + kA] = co[t1 * Q2 + kA] * g1 + co[t2 * Q2 + kA] * g2 + co[d * Q2 + kA] * gn;
         }
         __syncwarp();
     }
@@ -262,11 +275,12 @@ __device__ __forceinline__ void lift_slot(const LevelView<T>& L, const SlotInfo<
         T* X3 = X2 + Q * N;
         const T sgn = s.side == 0 ? T(1) : T(-1);
         for (int k = lane; k < Q2; k += 32) {
-            const T wS = wSp[k];
-            const T uA = m[k], dA = m[Q2 + k];
+            const int kA = mortar_index<Q>(s.o, k % Q, k / Q);
+            const T wS = wSp[kA];
+            const T uA = m[kA], dA = m[Q2 + kA];
             T jmp, avg, bc;
             if (interior) {
-                const T uB = m[2 * Q2 + k], dB = m[3 * Q2 + k];
+                const T uB = m[2 * Q2 + kA], dB = m[3 * Q2 + kA];
                 jmp = sgn * (uA - uB);
                 avg = T(0.5) * sgn * (dA + dB);
                 bc = T(-0.5) * wS * jmp;
@@ -277,9 +291,9 @@ __device__ __forceinline__ void lift_slot(const LevelView<T>& L, const SlotInfo<
             }
             const T b2 = bc * sgn;
             PA[k] = wS * (sig * jmp - avg);
-            PB1[k] = b2 * co[t1 * Q2 + k];
-            PB2[k] = b2 * co[t2 * Q2 + k];
-            PBn[k] = b2 * co[d * Q2 + k];
+            PB1[k] = b2 * co[t1 * Q2 + kA];
+            PB2[k] = b2 * co[t2 * Q2 + kA];
+            PBn[k] = b2 * co[d * Q2 + kA];
         }
         __syncwarp();
         const T* M2 = sFT + L.ft.off[N - kMinN][Q - kMinN][s.p1];
@@ -351,7 +365,8 @@ __host__ __device__ constexpr int table_vals(int ftot) {
 
 // One mortar slot of an element, packed so that a warp can hold the records of
 // all of an element's slots (one per lane) and broadcast them by shuffles:
-// info = face | side << 3 | pos0 << 4 | pos1 << 6 | q << 8 | interior << 12.
+// info = face | side << 3 | pos0 << 4 | pos1 << 6 | q << 8 | interior << 12 |
+// orientation << 13.
 template <typename T>
 struct SlotRec {
     int info;
@@ -366,7 +381,8 @@ __device__ __forceinline__ SlotRec<T> load_rec(const LevelView<T>& L, int si) {
     const int f = L.slot_face[si], side = L.slot_side[si];
     const int p0 = side == 0 ? M.posA0 : M.posB0, p1 = side == 0 ? M.posA1 : M.posB1;
     SlotRec<T> r;
-    r.info = f | side << 3 | p0 << 4 | p1 << 6 | (int)M.q << 8 | (M.eB >= 0 ? 1 << 12 : 0);
+    r.info = f | side << 3 | p0 << 4 | p1 << 6 | (int)M.q << 8 | (M.eB >= 0 ? 1 << 12 : 0) |
+             (side ? (int)M.orient << 13 : 0);
     r.goff = M.goff;
     r.sig = L.sigma[mi];
     return r;
@@ -380,6 +396,7 @@ __device__ __forceinline__ SlotInfo<T> unpack_rec(const SlotRec<T>& r) {
     s.p0 = (r.info >> 4) & 3;
     s.p1 = (r.info >> 6) & 3;
     s.q = (r.info >> 8) & 15;
+    s.o = (r.info >> 13) & 7;
     s.goff = r.goff;
     return s;
 }

@@ -236,10 +236,11 @@ int ensure_work(dg_ctx* c, int l) {
     return DG_OK;
 }
 
-void cheb_defaults(const dg_cheb_opts* o, int& ne, int& nc, double& Lam) {
+void cheb_defaults(const dg_cheb_opts* o, int& ne, int& nc, double& Lam, double& scale) {
     ne = (o && o->n_eigs > 0) ? o->n_eigs : 15;
     nc = (o && o->n_cheb > 0) ? o->n_cheb : 15;
     Lam = (o && o->Lambda > 0) ? o->Lambda : 20.0;
+    scale = (o && o->lam_scale > 0) ? o->lam_scale : 1.0;
     if (nc > kMaxCheb) nc = kMaxCheb;
 }
 
@@ -250,8 +251,8 @@ int smooth_t(dg_ctx* c, int l, const T* b, T* x, const dg_cheb_opts* o) {
     if (rc) return rc;
     if ((rc = ensure_dense(c, l))) return rc;
     int ne, nc;
-    double Lam;
-    cheb_defaults(o, ne, nc, Lam);
+    double Lam, scale;
+    cheb_defaults(o, ne, nc, Lam, scale);
     Work<T>& W = work_of<T>(c->lv[l]);
     const long long n = c->lv[l].h.n_dofs();
     cudaStream_t st = c->st;
@@ -266,7 +267,7 @@ int smooth_t(dg_ctx* c, int l, const T* b, T* x, const dg_cheb_opts* o) {
         CK(cg_p_update<T>(W.sm, W.p, W.r, n, st));
         c->launches += 3;
     }
-    CK(sm_cheb_coeffs(W.sm, nc, Lam, st));
+    CK(sm_cheb_coeffs(W.sm, nc, Lam, scale, st));
     CK(cudaMemsetAsync(W.p, 0, n * sizeof(T), st));
     c->launches += 1;
     for (int k = 0; k < nc; ++k) {
@@ -401,7 +402,7 @@ bool same_opts(const dg_mg_opts& a, const dg_mg_opts* b) {
     const dg_mg_opts z{};
     const dg_mg_opts& bb = b ? *b : z;
     return a.coarse == bb.coarse && a.cheb.n_eigs == bb.cheb.n_eigs && a.cheb.n_cheb == bb.cheb.n_cheb &&
-           a.cheb.Lambda == bb.cheb.Lambda;
+           a.cheb.Lambda == bb.cheb.Lambda && a.cheb.lam_scale == bb.cheb.lam_scale;
 }
 
 // The V-cycle of one FCG iteration (FP64: r -> v; FP32: fcg32[0] -> fcg32[1]).
@@ -456,6 +457,7 @@ int upload_level(dg_ctx* c, LevelDev& L, int li, std::string& err) {
     cudaStream_t st = c->st;
     LevelHost& h = L.h;
     L.leaves = A.upload(h.leaves, st);
+    L.block = A.upload(h.block, st);
     L.p = A.upload(h.p, st);
     L.dof_off = A.upload(h.dof_off, st);
     L.vqp_off = A.upload(h.vqp_off, st);
@@ -519,6 +521,9 @@ int upload_level(dg_ctx* c, LevelDev& L, int li, std::string& err) {
     }
     g.map_kind = c->desc.map_kind;
     g.warp_amp = c->desc.warp_amp;
+    g.n_blocks = (int)c->blocks.size();
+    g.blocks = c->blocks_dev;
+    g.block = L.block;
     cudaError_t e1 = launch_node_coords(g, X, st);
     cudaError_t e2 = launch_volume_geom(g, X, L.G64, L.wdetJ, L.vxyz, nv, bad, st);
     cudaError_t e3 = launch_mortar_geom(g, X, L.mortars, nmort, c->C, L.mg64, L.sigma64, L.bxyz, nb, bad, st);
@@ -544,23 +549,42 @@ int upload_level(dg_ctx* c, LevelDev& L, int li, std::string& err) {
 
 bool validate_desc(const dg_mesh_desc* d, std::string& err) {
     if (!d || d->n_elems <= 0 || !d->leaves || !d->p) { err = "mesh description is empty"; return false; }
-    for (int k = 0; k < 3; ++k)
-        if (!(d->hi[k] > d->lo[k])) { err = "box must have hi > lo"; return false; }
-    if (d->map_kind != DG_MAP_AFFINE && d->map_kind != DG_MAP_SINE_WARP) { err = "unknown map kind"; return false; }
+    if (d->n_blocks < 0) { err = "n_blocks must be >= 0"; return false; }
+    if (d->n_blocks == 0) {
+        for (int k = 0; k < 3; ++k)
+            if (!(d->hi[k] > d->lo[k])) { err = "box must have hi > lo"; return false; }
+        if (d->map_kind != DG_MAP_AFFINE && d->map_kind != DG_MAP_SINE_WARP) { err = "unknown map kind"; return false; }
+        return true;
+    }
+    if (d->n_blocks > 4096) { err = "at most 4096 blocks"; return false; }
+    if (!d->blocks || !d->elem_block) { err = "blocks and elem_block are required when n_blocks > 0"; return false; }
+    for (int b = 0; b < d->n_blocks; ++b) {
+        const dg_block& B = d->blocks[b];
+        if (B.kind == DG_BLOCK_HEX8) continue;
+        if (B.kind != DG_BLOCK_WEDGE && B.kind != DG_BLOCK_SHELL) { err = "unknown block kind"; return false; }
+        if (B.face < 0 || B.face > 5) { err = "block face must be 0..5"; return false; }
+        if (B.kind == DG_BLOCK_WEDGE && !(B.a > 0 && B.r > B.a)) { err = "wedge needs 0 < a < r"; return false; }
+        if (B.kind == DG_BLOCK_SHELL && !(B.r1 > 0 && B.r2 > B.r1)) { err = "shell needs 0 < r1 < r2"; return false; }
+    }
+    for (int e = 0; e < d->n_elems; ++e)
+        if (d->elem_block[e] < 0 || d->elem_block[e] >= d->n_blocks) { err = "element block index out of range"; return false; }
     return true;
 }
 
-int build_hierarchy(const dg_mesh_desc* d, std::vector<LevelHost>& levels, std::string& err) {
+int build_hierarchy(const dg_mesh_desc* d, std::vector<LevelHost>& levels, BlockTopo& topo, std::string& err) {
+    if (!build_block_topology(d->blocks, d->n_blocks > 0 ? d->n_blocks : 1, topo, err)) return DG_ERR_INVALID;
     LevelHost fine;
     fine.leaves.assign(d->leaves, d->leaves + 4 * (size_t)d->n_elems);
     fine.p.assign(d->p, d->p + d->n_elems);
-    if (!build_level_connectivity(fine, err)) return DG_ERR_INVALID;
+    if (d->n_blocks > 0) fine.block.assign(d->elem_block, d->elem_block + d->n_elems);
+    else fine.block.assign(d->n_elems, 0);
+    if (!build_level_connectivity(fine, topo, err)) return DG_ERR_INVALID;
     std::vector<LevelHost> fine_first;
     fine_first.push_back(std::move(fine));
     while (true) {
         LevelHost coarse;
         std::string e2;
-        if (!coarsen_level(fine_first.back(), coarse, e2)) {
+        if (!coarsen_level(fine_first.back(), coarse, topo, e2)) {
             if (!e2.empty()) { err = e2; return DG_ERR_INVALID; }
             break;
         }
@@ -596,7 +620,8 @@ int dg_ctx_footprint(const dg_mesh_desc* mesh, const dg_disc_opts* opts, size_t*
     std::string err;
     if (!validate_desc(mesh, err)) return fail(DG_ERR_INVALID, err);
     std::vector<LevelHost> lv;
-    int rc = build_hierarchy(mesh, lv, err);
+    BlockTopo topo;
+    int rc = build_hierarchy(mesh, lv, topo, err);
     if (rc) return fail(rc, err);
     size_t b = 2 * TabIndex::Count * kTabStride * 12;
     for (auto& h : lv) b += level_bytes(h);
@@ -612,7 +637,8 @@ int dg_ctx_create(const dg_mesh_desc* mesh, const dg_disc_opts* opts, void* stre
     std::string err;
     if (!validate_desc(mesh, err)) return fail(DG_ERR_INVALID, err);
     std::vector<LevelHost> lvh;
-    int rc = build_hierarchy(mesh, lvh, err);
+    BlockTopo topo;
+    int rc = build_hierarchy(mesh, lvh, topo, err);
     if (rc) return fail(rc, err);
     auto c = std::make_unique<dg_ctx>();
     c->st = (cudaStream_t)stream;
@@ -620,6 +646,10 @@ int dg_ctx_create(const dg_mesh_desc* mesh, const dg_disc_opts* opts, void* stre
     c->desc = *mesh;
     c->desc.leaves = nullptr;
     c->desc.p = nullptr;
+    if (mesh->n_blocks > 0) c->blocks.assign(mesh->blocks, mesh->blocks + mesh->n_blocks);
+    c->desc.blocks = nullptr;
+    c->desc.elem_block = nullptr;
+    c->topo = std::move(topo);
     std::vector<double> tab;
     build_tables(tab);
     std::vector<float> tabf(tab.begin(), tab.end());
@@ -630,6 +660,7 @@ int dg_ctx_create(const dg_mesh_desc* mesh, const dg_disc_opts* opts, void* stre
     std::vector<float> ftabf(ftab.begin(), ftab.end());
     c->ftab64 = c->arena.upload(ftab, c->st);
     c->ftab32 = c->arena.upload(ftabf, c->st);
+    if (!c->blocks.empty()) c->blocks_dev = c->arena.upload(c->blocks, c->st);
     c->red.partials = c->arena.alloc<double>(kRedBlocks * 4);
     c->red.out = c->arena.alloc<double>(4);
     c->red.counter = c->arena.alloc<unsigned>(1);
@@ -713,6 +744,15 @@ int dg_level_leaves(dg_ctx* c, int level, int* leaves, int* p, int64_t* dof_off)
     if (p) std::memcpy(p, h.p.data(), h.p.size() * sizeof(int));
     if (dof_off)
         for (size_t i = 0; i < h.dof_off.size(); ++i) dof_off[i] = h.dof_off[i];
+    return DG_OK;
+}
+
+int dg_level_blocks(dg_ctx* c, int level, int* elem_block) {
+    if (!c || !elem_block) return fail(DG_ERR_INVALID, "NULL argument");
+    level = resolve_level(c, level);
+    if (level < 0 || level >= (int)c->lv.size()) return fail(DG_ERR_INVALID, "level out of range");
+    const LevelHost& h = c->lv[level].h;
+    std::memcpy(elem_block, h.block.data(), h.block.size() * sizeof(int));
     return DG_OK;
 }
 

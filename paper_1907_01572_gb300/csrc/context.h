@@ -47,7 +47,7 @@ struct Work {
 
 struct LevelDev {
     LevelHost h;
-    int *leaves = nullptr, *p = nullptr;
+    int *leaves = nullptr, *p = nullptr, *block = nullptr;
     long long *dof_off = nullptr, *vqp_off = nullptr;
     Mortar* mortars = nullptr;
     int *slot_off = nullptr, *slot_mortar = nullptr;
@@ -85,6 +85,9 @@ struct dg_ctx {
     cudaStream_t st = nullptr;
     double C = 10.0;
     dg_mesh_desc desc{};
+    std::vector<dg_block> blocks;   // host copy of the mesh blocks (empty: single box)
+    dg::BlockTopo topo;
+    dg_block* blocks_dev = nullptr;
     std::vector<dg::LevelDev> lv;   // 0 = coarsest
     dg::Arena arena;
     double* tab64 = nullptr;

@@ -1,12 +1,17 @@
 // Geometry precompute on the device, FP64 (Sec. II.A.5):
 //  * node coordinates: the block map sampled at each element's LGL nodes
-//    (isoparametric elements, Phi_e linear in the block coordinates, eq. Phi_e);
+//    (Phi_e linear in the block coordinates, eq. Phi_e); on the single box the
+//    geometry is isoparametric (the node coordinates interpolated), on block
+//    meshes it is exact (x and J of the block map at every GL point);
 //  * volume GL points: J = dx/dxi of the degree-p interpolant, det J, J^-1 and
 //    the stiffness metric G_lm = w det J (J^-1)_l . (J^-1)_m of eq. (harald-stiff);
-//  * mortar GL points: S^m (eq. Surface-Jacobian) and the normal from side A,
-//    and per side c_l = (J^-1)_l . n_A, the factors turning reference gradients
+//  * mortar GL points (indexed in side A's face frame): S^m (eq.
+//    Surface-Jacobian) and the normal from side A, and per side
+//    c_l = (J^-1)_l . n_A (side B evaluated at the same point of its own,
+//    possibly turned, face frame), the factors turning reference gradients
 //    into the normal derivative; h = 2 J / S per side and point, and the penalty
 //    sigma = C p_m^2 / min h (eq. penaltyparameter).
+#include "blocks.h"
 #include "geom.h"
 
 namespace dg {
@@ -70,6 +75,26 @@ __device__ void jacobian_at(const double* X, int n, const double* xl, const doub
             }
 }
 
+// Geometry of element e at reference point xi: on block meshes the exact map
+// (block map composed with the element's linear map into its block, J scaled
+// by 2^-level); on the single box the isoparametric interpolant of the node
+// coordinates X.
+__device__ void elem_geom(const GeomArgs& g, const double* X, int e, const double xi[3], double J[3][3],
+                          double xp[3]) {
+    if (g.n_blocks > 0) {
+        const int* lf = g.leaves + 4 * e;
+        const double inv = 1.0 / (double)(1 << lf[0]);
+        double xb[3];
+        for (int d = 0; d < 3; ++d) xb[d] = -1.0 + (2.0 * lf[1 + d] + xi[d] + 1.0) * inv;
+        block_jacobian(g.blocks[g.block[e]], xb, J, xp);
+        for (int i = 0; i < 3; ++i)
+            for (int l = 0; l < 3; ++l) J[i][l] *= inv;
+        return;
+    }
+    const int n = g.p[e] + 1;
+    jacobian_at(X + 3 * g.dof_off[e], n, g.tab + tab_n(TabIndex::LGLx, n), xi, J, xp);
+}
+
 __device__ inline double inv3(const double J[3][3], double Ji[3][3]) {
     const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
                        J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
@@ -99,6 +124,19 @@ __global__ void node_coords_kernel(GeomArgs g, double* X) {
         lo[d] = g.lo[d] + w[d] * lf[1 + d];
     }
     double* Xe = X + 3 * g.dof_off[e];
+    if (g.n_blocks > 0) {   // block reference point of the node, then the block map
+        const dg_block& B = g.blocks[g.block[e]];
+        const double inv = 1.0 / (double)(1 << lf[0]);
+        for (int k = threadIdx.x; k < n3; k += blockDim.x) {
+            const int a = k % n, b = (k / n) % n, c = k / (n * n);
+            const double xi[3] = {xl[a], xl[b], xl[c]};
+            double xb[3], y[3];
+            for (int d = 0; d < 3; ++d) xb[d] = -1.0 + (2.0 * lf[1 + d] + xi[d] + 1.0) * inv;
+            block_point(B, xb, y);
+            for (int d = 0; d < 3; ++d) Xe[d * n3 + k] = y[d];
+        }
+        return;
+    }
     for (int k = threadIdx.x; k < n3; k += blockDim.x) {
         const int a = k % n, b = (k / n) % n, c = k / (n * n);
         const double xi[3] = {xl[a], xl[b], xl[c]};
@@ -120,16 +158,14 @@ __global__ void volume_geom_kernel(GeomArgs g, const double* X, double* G, doubl
     const int e = blockIdx.x;
     if (e >= g.n_elems) return;
     const int n = g.p[e] + 1, n3 = n * n * n;
-    const double* xl = g.tab + tab_n(TabIndex::LGLx, n);
     const double* xg = g.tab + tab_n(TabIndex::GLx, n);
     const double* wg = g.tab + tab_n(TabIndex::GLw, n);
-    const double* Xe = X + 3 * g.dof_off[e];
     const long long vo = g.vqp_off[e];
     for (int k = threadIdx.x; k < n3; k += blockDim.x) {
         const int i = k % n, j = (k / n) % n, l = k / (n * n);
         const double xi[3] = {xg[i], xg[j], xg[l]};
         double J[3][3], Ji[3][3], xp[3];
-        jacobian_at(Xe, n, xl, xi, J, xp);
+        elem_geom(g, X, e, xi, J, xp);
         const double det = inv3(J, Ji);
         if (!(det > 0.0)) atomicExch(bad, 1);
         const double wd = wg[i] * wg[j] * wg[l] * det;
@@ -160,7 +196,7 @@ __global__ void mortar_geom_kernel(GeomArgs g, const double* X, const Mortar* mo
         const int i1 = k % q, i2 = k / q;
         double nA[3];
         {   // side A: normal, surface Jacobian, metric
-            const int e = M.eA, n = g.p[e] + 1;
+            const int e = M.eA;
             const int d = M.fA >> 1, s = M.fA & 1;
             int t1, t2;
             tangential(d, t1, t2);
@@ -169,7 +205,7 @@ __global__ void mortar_geom_kernel(GeomArgs g, const double* X, const Mortar* mo
             xi[t1] = submap(M.posA0, sg[i1]);
             xi[t2] = submap(M.posA1, sg[i2]);
             double J[3][3], Ji[3][3], xp[3];
-            jacobian_at(X + 3 * g.dof_off[e], n, g.tab + tab_n(TabIndex::LGLx, n), xi, J, xp);
+            elem_geom(g, X, e, xi, J, xp);
             const double det = inv3(J, Ji);
             if (!(det > 0.0)) atomicExch(bad, 1);
             const double nrm = sqrt(Ji[d][0] * Ji[d][0] + Ji[d][1] * Ji[d][1] + Ji[d][2] * Ji[d][2]);
@@ -186,16 +222,17 @@ __global__ void mortar_geom_kernel(GeomArgs g, const double* X, const Mortar* mo
             }
         }
         if (M.eB >= 0) {
-            const int e = M.eB, n = g.p[e] + 1;
+            const int e = M.eB;
             const int d = M.fB >> 1, s = M.fB & 1;
             int t1, t2;
             tangential(d, t1, t2);
-            double xi[3];
+            double xi[3], b1, b2;
+            orient_coords(M.orient, sg[i1], sg[i2], b1, b2);   // this point in side B's face frame
             xi[d] = s ? 1.0 : -1.0;
-            xi[t1] = submap(M.posB0, sg[i1]);
-            xi[t2] = submap(M.posB1, sg[i2]);
+            xi[t1] = submap(M.posB0, b1);
+            xi[t2] = submap(M.posB1, b2);
             double J[3][3], Ji[3][3], xp[3];
-            jacobian_at(X + 3 * g.dof_off[e], n, g.tab + tab_n(TabIndex::LGLx, n), xi, J, xp);
+            elem_geom(g, X, e, xi, J, xp);
             const double det = inv3(J, Ji);
             if (!(det > 0.0)) atomicExch(bad, 1);
             const double nrm = sqrt(Ji[d][0] * Ji[d][0] + Ji[d][1] * Ji[d][1] + Ji[d][2] * Ji[d][2]);

@@ -15,6 +15,9 @@ struct GeomArgs {
     int map_kind;
     double warp_amp;
     int warp_k[3];
+    int n_blocks;               // 0: the box [lo, hi] with map_kind; else blocks[block[e]]
+    const dg_block* blocks;     // device, n_blocks
+    const int* block;           // device, per element
 };
 
 // X: 3 * n_dofs doubles, element block e at 3*dof_off[e]: [x(n^3), y(n^3), z(n^3)]

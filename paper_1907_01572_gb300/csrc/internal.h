@@ -66,13 +66,24 @@ struct Mortar {            // device record (32 bytes)
     unsigned char fA, fB;  // faces (2*dim + side)
     unsigned char posA0, posA1, posB0, posB1;  // sub-face codes along the two tangential axes
     unsigned char q;       // GL points per direction = p_m + 1
-    unsigned char pad;
+    unsigned char orient;  // side B's face frame relative to side A's (blocks.h orient_coords); 0 inside a block
     long long goff;        // offset (in points) into the mortar geometry arrays
     long long bnd_off;     // offset into boundary point arrays (-1 if interior)
 };
 
+// Neighbour of each block face: block nb's face nf with relative orientation
+// orient (blocks.h), or nb = -1 on the domain boundary.
+struct BlockFace {
+    int nb = -1, nf = 0, orient = 0;
+};
+struct BlockTopo {
+    int n_blocks = 1;
+    std::vector<BlockFace> face;     // 6 per block
+};
+
 struct LevelHost {
     std::vector<int> leaves;         // 4 per element
+    std::vector<int> block;          // block of each element
     std::vector<int> p;
     std::vector<long long> dof_off;  // n_elems + 1
     std::vector<long long> vqp_off;  // volume GL point offsets, n_elems + 1
@@ -95,10 +106,13 @@ struct LevelHost {
     std::vector<int> buckets[kMaxN + 1];  // element ids by n
 };
 
+// Block connectivity from the block maps: faces whose four corners coincide
+// are glued, with the orientation under which the corners match.
+bool build_block_topology(const dg_block* blocks, int n_blocks, BlockTopo& topo, std::string& err);
 // Builds the finest level's connectivity; returns false with a message on a malformed mesh.
-bool build_level_connectivity(LevelHost& L, std::string& err);
+bool build_level_connectivity(LevelHost& L, const BlockTopo& topo, std::string& err);
 // Coarsens `fine` into `coarse` (Sec. II.E.3); returns false when no family merges.
-bool coarsen_level(const LevelHost& fine, LevelHost& coarse, std::string& err);
+bool coarsen_level(const LevelHost& fine, LevelHost& coarse, const BlockTopo& topo, std::string& err);
 
 // ---- device level ------------------------------------------------------------------
 template <typename T>

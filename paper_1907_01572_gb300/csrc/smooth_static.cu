@@ -106,6 +106,7 @@ int smooth_static_t(dg_ctx* c, int l, const T* b, T* x, const dg_cheb_opts* o, u
     const int ne = (o && o->n_eigs > 0) ? o->n_eigs : 15;
     int nc = (o && o->n_cheb > 0) ? o->n_cheb : 15;
     const double Lam = (o && o->Lambda > 0) ? o->Lambda : 20.0;
+    const double scale = (o && o->lam_scale > 0) ? o->lam_scale : 1.0;
     if (nc > kMaxCheb) nc = kMaxCheb;
     const long long n = c->lv[l].h.n_dofs();
     T* r = reinterpret_cast<T*>(base);
@@ -127,7 +128,7 @@ int smooth_static_t(dg_ctx* c, int l, const T* b, T* x, const dg_cheb_opts* o, u
         CKS(cg_update_fused<T>(sm, x, r, p, Ap, n, red, st));
         CKS(cg_p_update<T>(sm, p, r, n, st));
     }
-    CKS(sm_cheb_coeffs(sm, nc, Lam, st));
+    CKS(sm_cheb_coeffs(sm, nc, Lam, scale, st));
     CKS(cudaMemsetAsync(p, 0, n * sizeof(T), st));
     for (int k = 0; k < nc; ++k) {
         CKS(launch_apply<T>(view, c->lv[l].buckets, x, Ap, st, &launches));

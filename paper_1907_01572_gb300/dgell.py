@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libdgell.so")
 DG_OK, DG_ERR_INVALID, DG_ERR_OOM, DG_ERR_CUDA, DG_ERR_NOT_CONVERGED, DG_ERR_BREAKDOWN, DG_ERR_UNSUPPORTED = range(7)
 DG_FP64, DG_FP32, DG_BF16 = 0, 1, 2
 DG_MAP_AFFINE, DG_MAP_SINE_WARP = 0, 1
+DG_BLOCK_HEX8, DG_BLOCK_WEDGE, DG_BLOCK_SHELL = 0, 1, 2
 
 
 class DgError(RuntimeError):
@@ -24,10 +25,17 @@ class DgError(RuntimeError):
         self.code = code
 
 
+class dg_block(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("face", ctypes.c_int), ("corners", (ctypes.c_double * 3) * 8),
+                ("a", ctypes.c_double), ("r", ctypes.c_double), ("r1", ctypes.c_double), ("r2", ctypes.c_double)]
+
+
 class dg_mesh_desc(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3), ("map_kind", ctypes.c_int),
                 ("warp_amp", ctypes.c_double), ("warp_k", ctypes.c_int * 3), ("n_elems", ctypes.c_int),
-                ("leaves", ctypes.POINTER(ctypes.c_int)), ("p", ctypes.POINTER(ctypes.c_int))]
+                ("leaves", ctypes.POINTER(ctypes.c_int)), ("p", ctypes.POINTER(ctypes.c_int)),
+                ("n_blocks", ctypes.c_int), ("blocks", ctypes.POINTER(dg_block)),
+                ("elem_block", ctypes.POINTER(ctypes.c_int))]
 
 
 class dg_disc_opts(ctypes.Structure):
@@ -41,7 +49,8 @@ class dg_level_info(ctypes.Structure):
 
 
 class dg_cheb_opts(ctypes.Structure):
-    _fields_ = [("n_eigs", ctypes.c_int), ("n_cheb", ctypes.c_int), ("Lambda", ctypes.c_double)]
+    _fields_ = [("n_eigs", ctypes.c_int), ("n_cheb", ctypes.c_int), ("Lambda", ctypes.c_double),
+                ("lam_scale", ctypes.c_double)]
 
 
 class dg_mg_opts(ctypes.Structure):
@@ -72,6 +81,7 @@ _SIGS = {
     "dg_ctx_footprint": ([ctypes.POINTER(dg_mesh_desc), ctypes.POINTER(dg_disc_opts), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "dg_level_info_get": ([_P, ctypes.c_int, ctypes.POINTER(dg_level_info)], ctypes.c_int),
     "dg_level_leaves": ([_P, ctypes.c_int, _P, _P, _P], ctypes.c_int),
+    "dg_level_blocks": ([_P, ctypes.c_int, _P], ctypes.c_int),
     "dg_quadrature_points": ([_P, ctypes.c_int, _P, _P], ctypes.c_int),
     "dg_apply": ([_P, ctypes.c_int, ctypes.c_int, _P, _P], ctypes.c_int),
     "dg_rhs": ([_P, _P, _P, _P], ctypes.c_int),
@@ -138,6 +148,30 @@ def make_mesh_desc(desc):
     leaves = np.ascontiguousarray(np.asarray(desc["leaves"], dtype=np.int32).reshape(-1, 4))
     p = np.ascontiguousarray(np.asarray(desc["p"], dtype=np.int32).ravel())
     d = dg_mesh_desc()
+    if desc.get("blocks"):
+        blocks = (dg_block * len(desc["blocks"]))()
+        kinds = {"hex8": DG_BLOCK_HEX8, "wedge": DG_BLOCK_WEDGE, "shell": DG_BLOCK_SHELL}
+        for i, b in enumerate(desc["blocks"]):
+            blocks[i].kind = kinds[b["kind"]]
+            if b["kind"] == "hex8":
+                for c in range(8):
+                    for k in range(3):
+                        blocks[i].corners[c][k] = float(b["corners"][c][k])
+            else:
+                blocks[i].face = int(b["face"])
+            blocks[i].a = float(b.get("a", 0.0))
+            blocks[i].r = float(b.get("r", 0.0))
+            blocks[i].r1 = float(b.get("r1", 0.0))
+            blocks[i].r2 = float(b.get("r2", 0.0))
+        eb = np.ascontiguousarray(np.asarray(desc["elem_block"], dtype=np.int32).ravel())
+        d.n_blocks = len(desc["blocks"])
+        d.blocks = ctypes.cast(blocks, ctypes.POINTER(dg_block))
+        d.elem_block = eb.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        d.n_elems = len(p)
+        d.leaves = leaves.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        d.p = p.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        d._keep = (leaves, p, blocks, eb)
+        return d
     for k in range(3):
         d.lo[k] = float(desc["lo"][k])
         d.hi[k] = float(desc["hi"][k])
@@ -167,12 +201,12 @@ def dg_ctx_footprint(desc, penalty_c=10.0):
     return b.value
 
 
-def cheb_opts(n_eigs=15, n_cheb=15, Lambda=20.0):
-    return dg_cheb_opts(n_eigs, n_cheb, Lambda)
+def cheb_opts(n_eigs=15, n_cheb=15, Lambda=20.0, lam_scale=1.0):
+    return dg_cheb_opts(n_eigs, n_cheb, Lambda, lam_scale)
 
 
-def mg_opts(n_eigs=15, n_cheb=15, Lambda=20.0, coarse=0):
-    return dg_mg_opts(cheb_opts(n_eigs, n_cheb, Lambda), coarse)
+def mg_opts(n_eigs=15, n_cheb=15, Lambda=20.0, coarse=0, lam_scale=1.0):
+    return dg_mg_opts(cheb_opts(n_eigs, n_cheb, Lambda, lam_scale), coarse)
 
 
 def solver_opts(tol=1e-10, max_iter=100, mg_prec=DG_FP64, use_mg=1, graph_mode=0, **mg):
@@ -218,6 +252,11 @@ class Context:
         off = np.zeros(ne + 1, dtype=np.int64)
         _check(lib().dg_level_leaves(self.h, level, leaves.ctypes.data, p.ctypes.data, off.ctypes.data))
         return leaves, p, off
+
+    def level_blocks(self, level=-1):
+        eb = np.zeros(self.level_info(level)["n_elems"], dtype=np.int32)
+        _check(lib().dg_level_blocks(self.h, level, eb.ctypes.data))
+        return eb
 
     def quadrature_points(self, level=-1):
         import torch

@@ -239,3 +239,131 @@ def puncture_mesh(punctures, R=24.0, level=3, refine=2, p_base=4, p_fine=6):
     maxL = max(lf[0] for lf in leaves)
     p = np.array([p_fine if lf[0] == maxL else p_base for lf in leaves], dtype=np.int32)
     return dict(lo=lo, hi=hi, leaves=np.array(leaves, dtype=np.int32), p=p, warp=None)
+
+
+# ---- multi-block meshes ------------------------------------------------------------
+# Block descriptions: dict(kind="hex8", corners=8 x 3) | dict(kind="wedge", face,
+# a, r) | dict(kind="shell", face, r1, r2); a mesh dict with blocks carries
+# "blocks", "elem_block" (per leaf), "leaves" (level, ix, iy, iz in the leaf's
+# block frame) and "p".
+def cube_rotations():
+    """The 24 proper rotations of the reference cube (signed permutation matrices)."""
+    import itertools
+    out = []
+    for perm in itertools.permutations(range(3)):
+        for signs in itertools.product((-1, 1), repeat=3):
+            R = np.zeros((3, 3))
+            for i in range(3):
+                R[i, perm[i]] = signs[i]
+            if np.linalg.det(R) > 0:
+                out.append(R)
+    return out
+
+
+def hex8_box(lo, hi, R=None):
+    """hex8 block of the box [lo, hi] whose reference frame is turned by the rotation R."""
+    lo, hi = np.asarray(lo, dtype=np.float64), np.asarray(hi, dtype=np.float64)
+    R = np.eye(3) if R is None else np.asarray(R, dtype=np.float64)
+    corners = []
+    for c in range(8):
+        xi = np.array([2 * (c & 1) - 1, 2 * ((c >> 1) & 1) - 1, 2 * ((c >> 2) & 1) - 1], dtype=np.float64)
+        corners.append(lo + 0.5 * (R @ xi + 1.0) * (hi - lo))
+    return dict(kind="hex8", corners=np.array(corners))
+
+
+def _block_mesh(blocks, per_block_leaves, p):
+    eb, lv = [], []
+    for b, leaves in enumerate(per_block_leaves):
+        eb += [b] * len(leaves)
+        lv += list(leaves)
+    return dict(blocks=blocks, elem_block=np.array(eb, dtype=np.int32), leaves=np.array(lv, dtype=np.int32),
+                p=np.asarray(p, dtype=np.int32))
+
+
+def block_pair_mesh(rot=5, level=1, refine_block=0, seed=0, pmin=2, pmax=5, refine_count=1):
+    """Two unit boxes side by side along x, the second with its reference frame
+    turned by cube_rotations()[rot]; in block refine_block the `refine_count`
+    elements nearest the point (1, 0, 0) of the interface x = 1 are refined
+    once (2:1 faces across the block interface); p ~ U{pmin..pmax} (seed)."""
+    R = cube_rotations()[rot]
+    blocks = [hex8_box((0, 0, 0), (1, 1, 1)), hex8_box((1, 0, 0), (2, 1, 1), R)]
+    per = [uniform_leaves(level), uniform_leaves(level)]
+    C = blocks[refine_block]["corners"]
+
+    def centre(lf):
+        L, i, j, k = lf
+        xi = -1.0 + (2.0 * np.array([i, j, k], dtype=np.float64) + 1.0) / (1 << L)
+        w = [0.5 * (1 - xi[0]), 0.5 * (1 + xi[0])], [0.5 * (1 - xi[1]), 0.5 * (1 + xi[1])], \
+            [0.5 * (1 - xi[2]), 0.5 * (1 + xi[2])]
+        return sum(w[0][c & 1] * w[1][(c >> 1) & 1] * w[2][(c >> 2) & 1] * C[c] for c in range(8))
+
+    dist = [np.linalg.norm(centre(lf) - np.array([1.0, 0.0, 0.0])) for lf in per[refine_block]]
+    chosen = set(tuple(per[refine_block][i]) for i in np.argsort(dist)[:refine_count])
+    per[refine_block] = morton_sort(refine(per[refine_block], lambda lf: tuple(lf) in chosen))
+    rng = np.random.default_rng(seed)
+    n = sum(len(v) for v in per)
+    return _block_mesh(blocks, per, rng.integers(pmin, pmax + 1, size=n))
+
+
+def cubed_sphere_blocks(a=2.0, r=10.0, r_out=None):
+    """Centre cube [-a, a]^3, six wedges out to the sphere of radius r and, if
+    r_out is given, six inverse-radius shell blocks from r to r_out (13 blocks)."""
+    blocks = [hex8_box((-a, -a, -a), (a, a, a))]
+    blocks += [dict(kind="wedge", face=f, a=a, r=r) for f in range(6)]
+    if r_out is not None:
+        blocks += [dict(kind="shell", face=f, r1=r, r2=r_out) for f in range(6)]
+    return blocks
+
+
+def cubed_sphere_mesh(level=1, a=2.0, r=10.0, r_out=None, seed=0, pmin=3, pmax=5, refine_wedge=None):
+    """Every block at `level`, p ~ U{pmin..pmax} (seed).  refine_wedge = (block,
+    count): the `count` first leaves (Morton order) of that wedge refined once,
+    giving 2:1 faces on wedge-wedge, wedge-cube and wedge-shell interfaces."""
+    blocks = cubed_sphere_blocks(a, r, r_out)
+    per = [uniform_leaves(level) for _ in blocks]
+    if refine_wedge is not None:
+        b, count = refine_wedge
+        chosen = set(per[b][:count])
+        per[b] = morton_sort(refine(per[b], lambda lf: tuple(lf) in chosen))
+    rng = np.random.default_rng(seed)
+    n = sum(len(v) for v in per)
+    return _block_mesh(blocks, per, rng.integers(pmin, pmax + 1, size=n))
+
+
+def star_sphere_mesh(level=3, refine=2, seed=3, p_cut=4, p_lo=5, p_hi=8, a=2.0, r=10.0, r_out=1e9):
+    """The density-jump star on the 13-block cubed sphere: centre cube of
+    half-width a, wedges out to r, inverse-radius shell to r_out; every block
+    at `level`; centre-cube cells cut by the spheres r = 0.5 and r = 1 refined
+    `refine` times (2:1 balanced inside the cube, at most one level finer than
+    the wedges on the cube faces); p = p_cut on the finest cut cells, p ~
+    U{p_lo..p_hi} (seed) elsewhere."""
+    blocks = cubed_sphere_blocks(a, r, r_out)
+    lo, hi = (-a, -a, -a), (a, a, a)
+    centre = uniform_leaves(level)
+
+    def cut(lf):
+        x0, x1 = _cell_bounds(lf, lo, hi)
+        dmin, dmax = _dist_range(x0, x1)
+        return any(dmin <= s <= dmax for s in (0.5, 1.0))
+
+    for _ in range(refine):
+        centre = balance_2to1(refine_(centre, cut))
+    for L, i, j, k in centre:
+        m = 1 << L
+        if (min(i, j, k) == 0 or max(i, j, k) == m - 1) and L > level + 1:
+            raise ValueError("refinement reaches the cube faces: raise `level` or lower `refine`")
+    centre = morton_sort(centre)
+    per = [centre] + [uniform_leaves(level) for _ in blocks[1:]]
+    rng = np.random.default_rng(seed)
+    maxL = max(lf[0] for lf in centre)
+    p = []
+    for b, leaves in enumerate(per):
+        for lf in leaves:
+            pv = int(rng.integers(p_lo, p_hi + 1))
+            p.append(p_cut if (b == 0 and lf[0] == maxL and cut(lf)) else pv)
+    return _block_mesh(blocks, per, p)
+
+
+def oracle_block_mesh_args(desc):
+    """Positional arguments for the oracle's BlockMesh constructor."""
+    return desc["blocks"], desc["elem_block"], desc["leaves"], desc["p"]

@@ -36,7 +36,7 @@ def test_binding_covers_the_header():
 
 def test_version_and_error_text(lib):
     from paper_1907_01572_gb300 import dgell
-    assert dgell.lib().dg_version() == 106
+    assert dgell.lib().dg_version() == 107
     assert isinstance(dgell.lib().dg_last_error(), bytes)
 
 
@@ -70,3 +70,41 @@ def test_footprint_host_only_and_invalid_meshes(lib):
     empty["p"] = np.zeros(0, dtype=np.int32)
     with pytest.raises(dgell.DgError):
         dgell.dg_ctx_footprint(empty)
+
+
+def test_block_meshes_host_validation(lib):
+    """Multi-block meshes (no GPU): every relative orientation of two glued
+    boxes and the 13-block cubed sphere are accepted; a 4:1 face across a
+    block interface, a bad block index and an unknown block kind are not."""
+    import numpy as np
+    from paper_1907_01572_gb300 import dgell, inputs
+    for rot in range(24):
+        for side in (0, 1):
+            d = inputs.block_pair_mesh(rot=rot, level=1, refine_block=side, seed=rot)
+            assert dgell.dg_ctx_footprint(d) > 0
+    assert dgell.dg_ctx_footprint(inputs.cubed_sphere_mesh(level=1, r_out=1e3, refine_wedge=(3, 2))) > 0
+    assert dgell.dg_ctx_footprint(inputs.star_sphere_mesh(level=2, refine=1)) > 0
+    # refine the interface element of block 0 twice: its grandchildren face a level-1 cell of block 1
+    d = inputs.block_pair_mesh(rot=7, level=1, refine_block=0)
+    lv = [tuple(x) for x in d["leaves"]]
+    eb = list(d["elem_block"])
+    tgt = [i for i, (b, lf) in enumerate(zip(eb, lv)) if b == 0 and lf[0] == 2 and lf[1] == 3][0]
+    L, i, j, k = lv[tgt]
+    kids = [(L + 1, 2 * i + (c & 1), 2 * j + ((c >> 1) & 1), 2 * k + ((c >> 2) & 1)) for c in range(8)]
+    bad = dict(blocks=d["blocks"], leaves=np.array(lv[:tgt] + kids + lv[tgt + 1:], dtype=np.int32),
+               elem_block=np.array(eb[:tgt] + [0] * 8 + eb[tgt + 1:], dtype=np.int32),
+               p=np.full(len(lv) + 7, 2, dtype=np.int32))
+    with pytest.raises(dgell.DgError) as e:
+        dgell.dg_ctx_footprint(bad)
+    assert e.value.code == dgell.DG_ERR_INVALID
+    wrong = dict(d)
+    wrong["elem_block"] = np.full(len(d["p"]), 2, dtype=np.int32)
+    with pytest.raises(dgell.DgError):
+        dgell.dg_ctx_footprint(wrong)
+    kind = dict(d)
+    kind["blocks"] = [dict(b) for b in d["blocks"]]
+    kind["blocks"][1]["kind"] = "shell"
+    kind["blocks"][1]["face"] = 0
+    kind["blocks"][1]["r1"], kind["blocks"][1]["r2"] = 2.0, 1.0
+    with pytest.raises(dgell.DgError):
+        dgell.dg_ctx_footprint(kind)

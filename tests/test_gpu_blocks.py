@@ -1,0 +1,120 @@
+"""GPU parity on multi-block meshes (every relative orientation of glued
+blocks, cubed-sphere wedges and inverse-radius shell, 2:1 faces across block
+interfaces) against the oracle: FP64 apply within 1e-12 relative L2 on every
+multigrid level the library builds, and solves against a direct solve of the
+oracle's assembled system."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from gpu_util import oracle_level_mesh, oracle_mesh, rel_l2
+from oracle import sipg
+from paper_1907_01572_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    assert torch.cuda.is_available()
+    return torch
+
+
+@pytest.mark.parametrize("rot", range(24))
+def test_apply_every_block_orientation(rot, torch):
+    from paper_1907_01572_gb300 import dgell
+    desc = inputs.block_pair_mesh(rot=rot, level=1, refine_block=rot % 2, seed=rot, pmin=2, pmax=4)
+    m = oracle_mesh(desc)
+    A = sipg.assemble(m, 10.0)
+    ctx = dgell.Context(desc)
+    x = inputs.random_vector(m.n_dofs, seed=rot)
+    xd = torch.tensor(x, device="cuda")
+    yd = torch.empty_like(xd)
+    ctx.apply(xd, yd)
+    assert rel_l2(yd.cpu().numpy(), A @ x) < 1e-12
+    y32 = torch.empty(m.n_dofs, dtype=torch.float32, device="cuda")
+    ctx.apply(xd.float(), y32)
+    assert rel_l2(y32.double().cpu().numpy(), A @ xd.float().double().cpu().numpy()) < 1e-5
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["sphere", "pair"])
+def test_block_hierarchy_levels_match_oracle(name, torch):
+    """Every level of the multigrid hierarchy (coarsening inside blocks, 2:1
+    rebalancing across block interfaces, coarse geometry) applies the same
+    operator as the oracle built on that level's leaves."""
+    from paper_1907_01572_gb300 import dgell
+    if name == "sphere":
+        desc = inputs.cubed_sphere_mesh(level=1, a=1.0, r=3.0, r_out=30.0, refine_wedge=(4, 4), pmin=2, pmax=3)
+    else:
+        desc = inputs.block_pair_mesh(rot=11, level=2, refine_block=1, seed=3, pmin=2, pmax=3, refine_count=5)
+    ctx = dgell.Context(desc)
+    nl = ctx.level_info()["n_levels"]
+    assert nl >= 2
+    for level in range(nl):
+        m = oracle_level_mesh(ctx, desc, level)
+        A = sipg.assemble(m, 10.0)
+        x = inputs.random_vector(m.n_dofs, seed=level)
+        xd = torch.tensor(x, device="cuda")
+        yd = torch.empty_like(xd)
+        ctx.apply(xd, yd, level=level)
+        assert rel_l2(yd.cpu().numpy(), A @ x) < 1e-12, level
+    ctx.close()
+
+
+def test_star_on_cubed_sphere_matches_direct_solve(torch):
+    """Density-jump star (-Lap u = 4 pi rho) on a small 13-block cubed sphere:
+    the GPU's multigrid-preconditioned FCG (FP64 and FP32 V-cycle) reaches 1e-10
+    and agrees with scipy's direct solve of the oracle's assembled system."""
+    from paper_1907_01572_gb300 import dgell
+    desc = inputs.cubed_sphere_mesh(level=1, a=2.0, r=6.0, r_out=20.0, seed=5, pmin=3, pmax=4)
+    m = oracle_mesh(desc)
+    A = sipg.assemble(m, 10.0)
+    F = sipg.rhs(m, inputs.star_source, inputs.star_solution, 10.0)
+    u_ref = spla.spsolve(A.tocsc(), F)
+    ctx = dgell.Context(desc)
+    xyz, bxyz = ctx.quadrature_points()
+    g = torch.tensor(inputs.star_source(xyz.T.cpu().numpy()), device="cuda")
+    gd = torch.tensor(inputs.star_solution(bxyz.T.cpu().numpy()), device="cuda")
+    Fd = torch.empty(m.n_dofs, dtype=torch.float64, device="cuda")
+    ctx.rhs(g, gd, Fd)
+    assert rel_l2(Fd.cpu().numpy(), F) < 1e-12
+    for prec in (dgell.DG_FP64, dgell.DG_FP32):
+        u = torch.zeros_like(Fd)
+        st = ctx.solve(Fd, u, tol=1e-10, max_iter=200, mg_prec=prec)
+        assert st["rel_residual"] < 1e-10
+        assert rel_l2(u.cpu().numpy(), u_ref) < 1e-8
+    ctx.close()
+
+
+def test_star_sphere_discretisation_error_decreases(torch):
+    """The star on the 13-block cubed sphere (inverse-radius shell to r = 20,
+    Dirichlet data from the closed form there): the L2 error of the GPU
+    solution against the closed form u(r) (oracle quadrature) falls when the
+    cells cut by the density jumps are refined."""
+    from paper_1907_01572_gb300 import dgell
+    errs = []
+    for level, refine in ((2, 0), (2, 1)):
+        desc = inputs.star_sphere_mesh(level=level, refine=refine, p_cut=4, p_lo=4, p_hi=5, r_out=20.0)
+        ctx = dgell.Context(desc)
+        xyz, bxyz = ctx.quadrature_points()
+        X = xyz.T.cpu().numpy()
+        g = torch.tensor(inputs.star_source(X), device="cuda")
+        gd = torch.tensor(inputs.star_solution(bxyz.T.cpu().numpy()), device="cuda")
+        n = ctx.level_info()["n_dofs"]
+        F = torch.empty(n, dtype=torch.float64, device="cuda")
+        ctx.rhs(g, gd, F)
+        u = torch.zeros_like(F)
+        st = ctx.solve(F, u, tol=1e-10, max_iter=300, mg_prec=dgell.DG_FP32)
+        assert st["rel_residual"] < 1e-10
+        m = oracle_mesh(desc)
+        errs.append(sipg.l2_error(m, u.cpu().numpy(), inputs.star_solution, extra=2))
+        ctx.close()
+    assert errs[1] < 0.7 * errs[0]

@@ -169,3 +169,34 @@ def test_wedge_and_shell_frames_right_handed():
             # the third reference axis points outward along the cube face normal
             d, s = divmod(f, 2)
             assert J[d, 2] * (1 if s else -1) > 0
+
+
+def test_block_jacobians_match_finite_differences():
+    blocks = [dict(kind="wedge", face=f, a=1.5, r=7.0) for f in range(6)]
+    blocks += [dict(kind="shell", face=f, r1=7.0, r2=1e6) for f in range(6)]
+    blocks += [dict(kind="hex8", corners=box_corners([0, 1, 2], [2, 2, 5], rotations()[9]))]
+    rng = np.random.default_rng(0)
+    xi = rng.uniform(-0.9, 0.9, size=(5, 3))
+    for blk in blocks:
+        J = blockmesh.block_jacobian(blk, xi)
+        for k in range(3):
+            h = 1e-6
+            fd = (blockmesh.block_map(blk, xi + h * np.eye(3)[k]) - blockmesh.block_map(blk, xi - h * np.eye(3)[k])) / (2 * h)
+            assert np.abs(J[:, :, k] - fd).max() <= 1e-6 * max(1.0, np.abs(fd).max())
+
+
+def test_far_shell_keeps_positive_jacobian_and_exact_volume():
+    """Shell to r2 = 1e9 in a single element per block at p = 2: the exact map
+    keeps det J > 0 (an interpolated map would fold), and the shell volume
+    between r1 and r2' matches 4/3 pi (r2'^3 - r1^3) for a moderate r2'."""
+    blocks = ball_blocks(1.0, 3.0, shell=1e9)
+    leaves = sum((uniform(0, b) for b in range(13)), [])
+    m = mesh_of(blocks, leaves, [2] * len(leaves))
+    for e in range(m.n_elems):
+        _, _, _, detJ, _ = sipg.volume_geometry(m, e)
+        assert np.all(detJ > 0)
+    blocks = ball_blocks(1.0, 3.0, shell=6.0)
+    m = mesh_of(blocks, leaves, [6] * len(leaves))
+    shell = sum(np.sum(sipg.volume_geometry(m, e, extra=4)[1] * sipg.volume_geometry(m, e, extra=4)[3])
+                for e in range(7, 13))
+    assert abs(shell / (4.0 / 3.0 * np.pi * (216.0 - 27.0)) - 1.0) < 1e-6
