@@ -335,18 +335,21 @@ def solve_bench(dgell, inputs, torch, n_solves=8):
     """Linear solves to 1e-10 relative residual (FP64 outer FCG) with the plain
     FP64 V-cycle and with the FP32 V-cycle, each V-cycle replayed as a CUDA graph
     on a dedicated stream: the 4^3 p=3 Poisson problem and the star with a
-    density jump (closed-form Dirichlet data); then the two-puncture Newton solve."""
+    density jump on the 13-block cubed sphere (centre cube a = 2, wedges to
+    r = 10, inverse-radius shell to r = 20, closed-form Dirichlet data); then
+    the two-puncture Newton solve."""
     import numpy as np
     out = {}
     stream = torch.cuda.Stream()
     cases = [
         ("poisson_4x4x4_p3", inputs.config1_mesh(),
          lambda X: 3 * np.pi ** 2 * np.sin(np.pi * X[:, 0]) * np.sin(np.pi * X[:, 1]) * np.sin(np.pi * X[:, 2]),
-         None),
-        ("star_density_jump", inputs.star_mesh(), inputs.star_source, inputs.star_solution),
+         None, n_solves),
+        ("star_cubed_sphere", inputs.star_sphere_mesh(level=2, refine=1, r_out=20.0), inputs.star_source,
+         inputs.star_solution, 3),
     ]
     with torch.cuda.stream(stream):
-        for name, desc, g, gD in cases:
+        for name, desc, g, gD, n_case in cases:
             ctx = dgell.Context(desc)
             info = ctx.level_info()
             xyz, bxyz = ctx.quadrature_points()
@@ -355,9 +358,11 @@ def solve_bench(dgell, inputs, torch, n_solves=8):
             F = torch.empty(info["n_dofs"], dtype=torch.float64, device="cuda")
             ctx.rhs(gq, gd, F)
             res = {"n_dofs": info["n_dofs"], "n_elems": info["n_elems"], "levels": info["n_levels"]}
+            if desc.get("blocks"):
+                res["blocks"] = len(desc["blocks"])
             for pname, prec in (("fp64", dgell.DG_FP64), ("mixed_fp32_vcycle", dgell.DG_FP32)):
                 lat, its, rr = [], [], []
-                for s in range(n_solves + 2):
+                for s in range(n_case + 2):
                     x = torch.zeros_like(F)
                     stream.synchronize()
                     t = time.perf_counter()
