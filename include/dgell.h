@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define DGELL_VERSION 107
+#define DGELL_VERSION 108
 
 enum {
     DG_OK = 0,

@@ -154,13 +154,27 @@ struct SlotInfo {
 };
 
 // Index, in the mortar's point order (side A's face frame), of the point at
-// (j1, j2) of this side's own Q x Q face grid; the GL points are symmetric, so
-// a mirrored axis maps j to Q - 1 - j.
+// (j1, j2) of this side's own Q x Q face grid, as c0 + c1 j1 + c2 j2: the GL
+// points are symmetric, so a mirrored axis maps j to Q - 1 - j, and a swap
+// exchanges the roles of the two axes.
 template <int Q>
-__device__ __forceinline__ int mortar_index(int o, int j1, int j2) {
-    const int w1 = (o & 2) ? Q - 1 - j1 : j1, w2 = (o & 4) ? Q - 1 - j2 : j2;
-    return (o & 1) ? w2 + Q * w1 : w1 + Q * w2;
-}
+struct MortarMap {
+    int c0, c1, c2;
+    __device__ __forceinline__ explicit MortarMap(int o) {
+        const int a1 = (o & 2) ? Q - 1 : 0, b1 = (o & 2) ? -1 : 1;
+        const int a2 = (o & 4) ? Q - 1 : 0, b2 = (o & 4) ? -1 : 1;
+        if (o & 1) {
+            c0 = a2 + Q * a1;
+            c1 = Q * b1;
+            c2 = b2;
+        } else {
+            c0 = a1 + Q * a2;
+            c1 = b1;
+            c2 = Q * b2;
+        }
+    }
+    __device__ __forceinline__ int operator()(int j1, int j2) const { return c0 + c1 * j1 + c2 * j2; }
+};
 
 template <typename T>
 __device__ __forceinline__ SlotInfo<T> slot_info(const LevelView<T>& L, int si) {
@@ -179,8 +193,8 @@ __device__ __forceinline__ SlotInfo<T> slot_info(const LevelView<T>& L, int si) 
 // Own trace at the Q x Q mortar points: u and dn = c^side . grad_xi u (c^side =
 // J^-1 n_A, three Q^2 blocks at co).  Mortar tables are (Im, Dm) pairs.  The
 // side works on its own face grid; per-point data and the trace buffer are in
-// the mortar's point order (side A's frame), reached through mortar_index.
-template <int N, int Q, typename T>
+// the mortar's point order (side A's frame), reached through MortarMap.
+template <int N, int Q, typename T, bool OR = true>
 __device__ __forceinline__ void trace_slot(const LevelView<T>& L, const SlotInfo<T>& s, const T* __restrict__ U,
                                            const T* __restrict__ sDL, const T* __restrict__ sFT, T* F,
                                            const T* __restrict__ co, T* __restrict__ mt, int lane) {
@@ -230,8 +244,9 @@ __device__ __forceinline__ void trace_slot(const LevelView<T>& L, const SlotInfo
         __syncwarp();
         const T* M2 = sFT + L.ft.off[N - kMinN][Q - kMinN][s.p1];
         T* out = mt + 4 * s.goff + 2 * s.side * Q2;
+        const MortarMap<Q> toA(OR ? s.o : 0);
         for (int k = lane; k < Q2; k += 32) {
-            const int i1 = k % Q, i2 = k / Q, kA = mortar_index<Q>(s.o, i1, i2);
+            const int i1 = k % Q, i2 = k / Q, kA = OR ? toA(i1, i2) : k;
             T u = 0, g1 = 0, g2 = 0, gn = 0;
 #pragma unroll
             for (int b = 0; b < N; ++b) {
@@ -253,7 +268,7 @@ __device__ __forceinline__ void trace_slot(const LevelView<T>& L, const SlotInfo
 // Flux at the mortar points and lift into Y for one mortar of the element.  Per
 // mortar point: surface weight wSp, this side's c (three Q^2 blocks at co) and
 // the trace buffer entries m = [u_A, dn_A, u_B, dn_B] (Q^2 each).
-template <int N, int Q, typename T>
+template <int N, int Q, typename T, bool OR = true>
 __device__ __forceinline__ void lift_slot(const LevelView<T>& L, const SlotInfo<T>& s, bool interior, T sig,
                                           T* __restrict__ Y, const T* __restrict__ sDL, const T* __restrict__ sFT,
                                           T* F, const T* __restrict__ wSp, const T* __restrict__ co,
@@ -274,8 +289,9 @@ __device__ __forceinline__ void lift_slot(const LevelView<T>& L, const SlotInfo<
         T* X2 = X1 + Q * N;
         T* X3 = X2 + Q * N;
         const T sgn = s.side == 0 ? T(1) : T(-1);
+        const MortarMap<Q> toA(OR ? s.o : 0);
         for (int k = lane; k < Q2; k += 32) {
-            const int kA = mortar_index<Q>(s.o, k % Q, k / Q);
+            const int kA = OR ? toA(k % Q, k / Q) : k;
             const T wS = wSp[kA];
             const T uA = m[kA], dA = m[Q2 + kA];
             T jmp, avg, bc;
@@ -484,7 +500,7 @@ __device__ __forceinline__ T* load_tables(const LevelView<T>& L, const T*& sFT, 
 
 // Warp per element; every element's slot records are fetched once (a lane per
 // slot) instead of through a dependent load chain per slot.
-template <int N, typename T, typename TX>
+template <int N, typename T, typename TX, bool OR = true>
 __device__ __forceinline__ void trace_body(const LevelView<T>& L, const int* __restrict__ bucket, int count,
                                            const TX* __restrict__ x, T* __restrict__ mt, int blk, int nblk) {
     using Ly = Layout<N>;
@@ -506,18 +522,20 @@ __device__ __forceinline__ void trace_body(const LevelView<T>& L, const int* __r
         for (int si = ws.s0; si < ws.s1; ++si) {
             const SlotInfo<T> s = unpack_rec(ws.get(si));
             const T* co = L.mg + 7 * s.goff + (s.side == 0 ? 1 : 4) * s.q * s.q;
-            DG_Q_SWITCH(s.q, (trace_slot<N, Q, T>(L, s, U, sDL, sFT, F, co, mt, lane)))
+            DG_Q_SWITCH(s.q, (trace_slot<N, Q, T, OR>(L, s, U, sDL, sFT, F, co, mt, lane)))
         }
     }
 }
 
-template <int N, typename T, typename TX>
+// OR: the level has mortars whose side B face frame is turned (block meshes);
+// without it the mortar-point permutation is compiled out.
+template <int N, typename T, typename TX, bool OR>
 __global__ void trace_kernel(LevelView<T> L, const int* __restrict__ bucket, int count, const TX* __restrict__ x,
                              T* __restrict__ mt) {
-    trace_body<N, T, TX>(L, bucket, count, x, mt, blockIdx.x, gridDim.x);
+    trace_body<N, T, TX, OR>(L, bucket, count, x, mt, blockIdx.x, gridDim.x);
 }
 
-template <int N, typename T, typename TX>
+template <int N, typename T, typename TX, bool OR = true>
 __device__ __forceinline__ void element_body(const LevelView<T>& L, const int* __restrict__ bucket, int count,
                                              const TX* __restrict__ x, T* __restrict__ y, int blk, int nblk) {
     using Ly = Layout<N>;
@@ -597,7 +615,7 @@ __device__ __forceinline__ void element_body(const LevelView<T>& L, const int* _
             const bool interior = (r.info >> 12) & 1;
             const T* mg = L.mg + 7 * s.goff;
             const T* co = mg + (s.side == 0 ? 1 : 4) * s.q * s.q;
-            DG_Q_SWITCH(s.q, (lift_slot<N, Q, T>(L, s, interior, r.sig, Y, sDL, sFT, F, mg, co, L.mt + 4 * s.goff,
+            DG_Q_SWITCH(s.q, (lift_slot<N, Q, T, OR>(L, s, interior, r.sig, Y, sDL, sFT, F, mg, co, L.mt + 4 * s.goff,
                                                  lane)))
         }
         for (int k = lane; k < N3; k += 32) y[dofo + k] = Y[k];
@@ -605,10 +623,10 @@ __device__ __forceinline__ void element_body(const LevelView<T>& L, const int* _
     }
 }
 
-template <int N, typename T, typename TX>
+template <int N, typename T, typename TX, bool OR>
 __global__ void element_kernel(LevelView<T> L, const int* __restrict__ bucket, int count, const TX* __restrict__ x,
                                T* __restrict__ y) {
-    element_body<N, T, TX>(L, bucket, count, x, y, blockIdx.x, gridDim.x);
+    element_body<N, T, TX, OR>(L, bucket, count, x, y, blockIdx.x, gridDim.x);
 }
 
 // All degree buckets of a level in one launch (used on small levels, where
@@ -835,35 +853,35 @@ inline int grid_cap() {
     return g;
 }
 
-template <int N, typename T, typename TX>
+template <int N, typename T, typename TX, bool OR>
 cudaError_t launch_trace(const LevelView<T>& L, const BucketInfo& b, const TX* x, cudaStream_t st) {
     using Ly = Layout<N>;
     static int W = 0, per_sm = 1;
     static size_t smem = 0;
     if (W == 0) {
         const size_t table_bytes = table_vals<N>(sizeof(T) == 4 ? L.ft.total : 0) * sizeof(T);
-        cudaError_t err = pick_warps(trace_kernel<N, T, TX>, table_bytes, Ly::TWARP * sizeof(T), W, smem, per_sm);
+        cudaError_t err = pick_warps(trace_kernel<N, T, TX, OR>, table_bytes, Ly::TWARP * sizeof(T), W, smem, per_sm);
         if (err != cudaSuccess) return err;
     }
     int grid = (b.count + W - 1) / W;
     if (grid > grid_cap() * per_sm) grid = grid_cap() * per_sm;
-    trace_kernel<N, T, TX><<<grid, W * 32, smem, st>>>(L, b.elems, b.count, x, L.mt);
+    trace_kernel<N, T, TX, OR><<<grid, W * 32, smem, st>>>(L, b.elems, b.count, x, L.mt);
     return cudaGetLastError();
 }
 
-template <int N, typename T, typename TX>
+template <int N, typename T, typename TX, bool OR>
 cudaError_t launch_element(const LevelView<T>& L, const BucketInfo& b, const TX* x, T* y, cudaStream_t st) {
     using Ly = Layout<N>;
     static int W = 0, per_sm = 1;
     static size_t smem = 0;
     if (W == 0) {
         const size_t table_bytes = table_vals<N>(sizeof(T) == 4 ? L.ft.total : 0) * sizeof(T);
-        cudaError_t err = pick_warps(element_kernel<N, T, TX>, table_bytes, Ly::EWARP * sizeof(T), W, smem, per_sm);
+        cudaError_t err = pick_warps(element_kernel<N, T, TX, OR>, table_bytes, Ly::EWARP * sizeof(T), W, smem, per_sm);
         if (err != cudaSuccess) return err;
     }
     int grid = (b.count + W - 1) / W;
     if (grid > grid_cap() * per_sm) grid = grid_cap() * per_sm;
-    element_kernel<N, T, TX><<<grid, W * 32, smem, st>>>(L, b.elems, b.count, x, y);
+    element_kernel<N, T, TX, OR><<<grid, W * 32, smem, st>>>(L, b.elems, b.count, x, y);
     return cudaGetLastError();
 }
 
@@ -1007,10 +1025,14 @@ cudaError_t launch_path(int path, const LevelView<T>& L, const BucketInfo* bucke
             const cudaStream_t sj = k == 0 ? st : as->side[k - 1];
             const BucketInfo& b = buckets[n];
             cudaError_t err = cudaSuccess;
-            if (phase == 0) {
-                DG_N_SWITCH(n, (err = apply_detail::launch_trace<NN, T, TX>(L, b, x, sj)))
+            if (phase == 0 && L.oriented) {
+                DG_N_SWITCH(n, (err = apply_detail::launch_trace<NN, T, TX, true>(L, b, x, sj)))
+            } else if (phase == 0) {
+                DG_N_SWITCH(n, (err = apply_detail::launch_trace<NN, T, TX, false>(L, b, x, sj)))
+            } else if (L.oriented) {
+                DG_N_SWITCH(n, (err = apply_detail::launch_element<NN, T, TX, true>(L, b, x, y, sj)))
             } else {
-                DG_N_SWITCH(n, (err = apply_detail::launch_element<NN, T, TX>(L, b, x, y, sj)))
+                DG_N_SWITCH(n, (err = apply_detail::launch_element<NN, T, TX, false>(L, b, x, y, sj)))
             }
             if (err != cudaSuccess) return err;
             if (launches) ++*launches;

@@ -99,6 +99,7 @@ LevelView<double> view<double>(dg_ctx* c, int l) {
     v.ftab = c->ftab64;
     v.ft = c->ft;
     v.ob_total = (long long)L.ob_count;
+    v.oriented = L.oriented;
     v.chk = device_check_flag();
     v.mt = L.mt64;
     return v;
@@ -127,6 +128,7 @@ LevelView<float> view<float>(dg_ctx* c, int l) {
     v.ftab = c->ftab32;
     v.ft = c->ft;
     v.ob_total = (long long)L.ob_count;
+    v.oriented = L.oriented;
     v.chk = device_check_flag();
     v.mt = L.mt32;
     return v;
@@ -462,6 +464,9 @@ int upload_level(dg_ctx* c, LevelDev& L, int li, std::string& err) {
     L.dof_off = A.upload(h.dof_off, st);
     L.vqp_off = A.upload(h.vqp_off, st);
     L.mortars = A.upload(h.mortars, st);
+    L.oriented = 0;
+    for (const Mortar& m : h.mortars)
+        if (m.orient) L.oriented = 1;
     L.slot_off = A.upload(h.slot_off, st);
     L.slot_mortar = A.upload(h.slot_mortar, st);
     L.slot_face = A.upload(h.slot_face, st);

@@ -48,6 +48,7 @@ struct Work {
 struct LevelDev {
     LevelHost h;
     int *leaves = nullptr, *p = nullptr, *block = nullptr;
+    int oriented = 0;                 // some mortar has a turned side B (block interfaces)
     long long *dof_off = nullptr, *vqp_off = nullptr;
     Mortar* mortars = nullptr;
     int *slot_off = nullptr, *slot_mortar = nullptr;

@@ -136,6 +136,7 @@ struct LevelView {         // passed by value to kernels
     const T* ftab;         // compact mortar tables (FaceTabs layout)
     FaceTabs ft;
     long long ob_total;    // entries of Ob (bounds check)
+    int oriented;          // some mortar of the level has a turned side B (Mortar::orient != 0)
     int* chk;              // self-check flag
     T* mt;                 // mortar trace buffer: 4 * n_mortar_pts ([u_A, dn_A, u_B, dn_B] per mortar)
 };

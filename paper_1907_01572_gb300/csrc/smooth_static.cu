@@ -91,6 +91,7 @@ LevelView<T> static_view(dg_ctx* c, int l) {
     }
     v.ft = c->ft;
     v.ob_total = (long long)L.ob_count;
+    v.oriented = L.oriented;
     v.chk = device_check_flag();
     return v;
 }
