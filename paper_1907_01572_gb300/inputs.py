@@ -367,3 +367,54 @@ def star_sphere_mesh(level=3, refine=2, seed=3, p_cut=4, p_lo=5, p_hi=8, a=2.0, 
 def oracle_block_mesh_args(desc):
     """Positional arguments for the oracle's BlockMesh constructor."""
     return desc["blocks"], desc["elem_block"], desc["leaves"], desc["p"]
+
+
+def _cell_points(block, lf):
+    """Physical corners and centre of a leaf of a block (cell selection only)."""
+    L, i, j, k = lf
+    pts = []
+    for c in range(9):
+        off = np.array([c & 1, (c >> 1) & 1, (c >> 2) & 1], dtype=np.float64) if c < 8 else np.full(3, 0.5)
+        xi = -1.0 + 2.0 * (np.array([i, j, k], dtype=np.float64) + off) / (1 << L)
+        if block["kind"] == "hex8":
+            C = np.asarray(block["corners"], dtype=np.float64)
+            w = [(0.5 * (1 - xi[0]), 0.5 * (1 + xi[0])), (0.5 * (1 - xi[1]), 0.5 * (1 + xi[1])),
+                 (0.5 * (1 - xi[2]), 0.5 * (1 + xi[2]))]
+            pts.append(sum(w[0][q & 1] * w[1][(q >> 1) & 1] * w[2][(q >> 2) & 1] * C[q] for q in range(8)))
+            continue
+        d, s = divmod(int(block["face"]), 2)
+        t1, t2 = ((d + 1) % 3, (d + 2) % 3) if s else ((d + 2) % 3, (d + 1) % 3)
+        v = np.zeros(3)
+        v[d] = 1.0 if s else -1.0
+        v[t1], v[t2] = xi[0], xi[1]
+        t = 0.5 * (xi[2] + 1.0)
+        u = v / np.linalg.norm(v)
+        if block["kind"] == "wedge":
+            pts.append((1 - t) * block["a"] * v + t * block["r"] * u)
+        else:
+            pts.append(u / ((1 - t) / block["r1"] + t / block["r2"]))
+    return np.array(pts)
+
+
+def puncture_sphere_mesh(punctures, level=2, a=2.0, r=10.0, r_out=20.0, p_base=4, p_fine=6):
+    """Puncture initial data on the 13-block cubed sphere (centre cube a, wedges
+    to r, inverse-radius shell to r_out, u = 0 there): every block at `level`,
+    the cells whose bounding box (grown by a quarter of its size) holds a
+    puncture refined once (2:1 across block interfaces at most), p_fine on the
+    refined cells, p_base elsewhere."""
+    blocks = cubed_sphere_blocks(a, r, r_out)
+    cs = [np.asarray(c, dtype=np.float64) for (_, c, _) in punctures]
+    per, p = [], []
+    for blk in blocks:
+        leaves = uniform_leaves(level)
+
+        def near(lf):
+            P = _cell_points(blk, lf)
+            lo, hi = P.min(axis=0), P.max(axis=0)
+            grow = 0.25 * (hi - lo)
+            return any(np.all(c >= lo - grow) and np.all(c <= hi + grow) for c in cs)
+
+        leaves = morton_sort(refine(leaves, near))
+        per.append(leaves)
+        p += [p_fine if lf[0] > level else p_base for lf in leaves]
+    return _block_mesh(blocks, per, p)
