@@ -22,9 +22,13 @@ import numpy as np
 from . import dgell, inputs
 
 
-def make_requests(n=32, rate_hz=20.0, seed=2):
+def make_requests(n=32, rate_hz=20.0, seed=2, full=False):
     """Seeded mix of Poisson (manufactured sine), star and puncture requests
-    with Poisson-process arrival times."""
+    with Poisson-process arrival times.  full=False: small meshes (Poisson
+    4^3-8^3 elements, p 3..5; star and punctures on box meshes).  full=True:
+    the served workload's sizes -- Poisson 4^3-16^3 elements with p 3..8
+    (4e3 to 3e6 DOFs), the density-jump star and the two punctures on the
+    13-block cubed sphere (shell to r = 20; 1.5e5 to 4.4e5 DOFs)."""
     rng = np.random.default_rng(seed)
     t = 0.0
     reqs = []
@@ -32,21 +36,30 @@ def make_requests(n=32, rate_hz=20.0, seed=2):
         t += rng.exponential(1.0 / rate_hz)
         kind = rng.choice(["poisson", "star", "puncture"], p=[0.5, 0.3, 0.2])
         if kind == "poisson":
-            level = int(rng.integers(2, 4))
-            p = int(rng.integers(3, 6))
+            level = int(rng.integers(2, 5 if full else 4))
+            p = int(rng.integers(3, 9 if full else 6))
             lv = inputs.uniform_leaves(level)
             desc = dict(lo=(-1.0, -1.0, -1.0), hi=(1.0, 1.0, 1.0), leaves=np.array(lv, dtype=np.int32),
                         p=np.full(len(lv), p, dtype=np.int32), warp=None)
             key = ("poisson", level, p)
             params = dict(amp=float(rng.uniform(0.5, 2.0)))
         elif kind == "star":
-            desc = inputs.star_mesh(level=3, refine=1, seed=3, p_lo=4, p_hi=6)
-            key = ("star", 3, 1)
+            if full:
+                refine = int(rng.integers(0, 2))
+                desc = inputs.star_sphere_mesh(level=2, refine=refine, r_out=20.0)
+                key = ("star_sphere", 2, refine)
+            else:
+                desc = inputs.star_mesh(level=3, refine=1, seed=3, p_lo=4, p_hi=6)
+                key = ("star", 3, 1)
             params = dict(amp=float(rng.uniform(0.5, 2.0)))
         else:
             punc = inputs.two_punctures()
-            desc = inputs.puncture_mesh(punc, refine=1, p_fine=5)
-            key = ("puncture", 1)
+            if full:
+                desc = inputs.puncture_sphere_mesh(punc, level=2)
+                key = ("puncture_sphere", 2)
+            else:
+                desc = inputs.puncture_mesh(punc, refine=1, p_fine=5)
+                key = ("puncture", 1)
             s = float(rng.uniform(0.5, 1.5))
             params = dict(punctures=[(m, c, tuple(s * np.asarray(P))) for (m, c, P) in punc])
         reqs.append(dict(id=i, kind=str(kind), key=key, desc=desc, params=params, arrival=t))
@@ -81,7 +94,8 @@ class Server:
         if req["kind"] == "puncture":
             ctx.puncture_setup(req["params"]["punctures"])
             u = torch.zeros(n, dtype=torch.float64, device="cuda")
-            steps, rn = ctx.newton_solve(u, tol_newton=1e-9, max_newton=12, mg_prec=self.mg_prec, tol=self.tol)
+            steps, rn = ctx.newton_solve(u, tol_newton=1e-9, max_newton=12, mg_prec=self.mg_prec, tol=self.tol,
+                                         max_iter=300)
             stream.synchronize()
             return u, {"newton_steps": steps, "residual_norm": rn}
         xyz, bxyz = ctx.quadrature_points()
