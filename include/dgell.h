@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define DGELL_VERSION 108
+#define DGELL_VERSION 109
 
 enum {
     DG_OK = 0,
@@ -270,13 +270,29 @@ typedef struct {
  * them in the context for dg_newton_*. */
 int dg_puncture_setup(dg_ctx* ctx, const dg_puncture_params* params);
 
-/* Weak residual R(u) (device double, n_dofs) of the puncture equation. */
+/* Weak residual R(u) (device double, n_dofs) of the puncture equation
+ * (DG_ERR_INVALID unless the puncture problem is the one set up last). */
 int dg_puncture_residual(dg_ctx* ctx, const double* u, double* R);
 
-/* One Newton step (Alg. 1): sets the Jacobian's zeroth-order term
- * 7 alpha beta (1 + alpha (1 + u))^-8, solves J du = -R(u) with dg_solve and
- * updates u += du.  u: device double, n_dofs.  residual_norm_out: host,
- * ||R(u)||_2 before the step (may be NULL). */
+/* Power-law source (the constant-density star of Sec. III.C,
+ * Lap psi + 2 pi rho psi^5 = 0, in the coercive form):
+ * R(u) = L u - F - int c u^power v, Jacobian zeroth-order term
+ * -power c u^(power-1),
+ * with the nonlinearity evaluated at the volume GL points (as the paper
+ * does for that problem).  coef_qp: device double, c at the finest level's
+ * volume GL points (dg_quadrature_points order), copied; power: 1..9; F:
+ * device double n_dofs forcing vector (e.g. dg_rhs with g = 0 for the
+ * Dirichlet data), copied, or NULL.  Makes this the problem of dg_newton_*. */
+int dg_power_source_setup(dg_ctx* ctx, const double* coef_qp, int power, const double* F);
+
+/* Weak residual R(u) of the nonlinear problem set up last (puncture or
+ * power-law source). */
+int dg_nonlinear_residual(dg_ctx* ctx, const double* u, double* R);
+
+/* One Newton step (Alg. 1) on the nonlinear problem set up last: sets the
+ * Jacobian's zeroth-order term (puncture: 7 alpha beta (1 + alpha (1 + u))^-8),
+ * solves J du = -R(u) with dg_solve and updates u += du.  u: device double,
+ * n_dofs.  residual_norm_out: host, ||R(u)||_2 before the step (may be NULL). */
 int dg_newton_step(dg_ctx* ctx, double* u, const dg_solver_opts* opts, dg_solve_stats* stats,
                    double* residual_norm_out);
 

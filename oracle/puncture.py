@@ -18,6 +18,11 @@ Readings:
 Pins: single-puncture closed form A_ij A^ij = 9 / (2 r^4) (|P|^2 + 2 (P.n)^2),
 J_R v against a central finite difference of R, quadratic Newton
 convergence (tests/test_oracle_puncture.py).
+
+PowerSourceProblem (the constant-density star of Sec. III.C) is pinned by its
+closed-form solution (tests/test_oracle_star.py): the discrete Newton solution
+converges to it under refinement, the Jacobian matches finite differences of
+the residual and Newton converges quadratically.
 """
 import numpy as np
 
@@ -96,3 +101,39 @@ def newton(prob, u0, lsolve, tol=1e-10, max_iter=20):
         u = u + du
         k += 1
     return u, k, hist
+
+
+class PowerSourceProblem:
+    """Power-law source (Sec. III.C, constant-density star Lap psi + 2 pi rho
+    psi^5 = 0 in the coercive form): R(u) = L u - F - int c u^k v with the
+    nonlinearity evaluated at the volume GL points after interpolating u
+    there; the Jacobian's zeroth-order coefficient is -k c u^(k-1) (J = L -
+    k c u^(k-1) mass, the source growing with u).  c: callable on points (P, 3);
+    F: forcing vector (Dirichlet lift), e.g. sipg.rhs with g = 0."""
+
+    def __init__(self, mesh, coef, power, F, C=10.0):
+        self.mesh = mesh
+        self.C = C
+        self.k = int(power)
+        self.F = np.asarray(F, dtype=np.float64)
+        self.L = sipg.assemble(mesh, C)
+        self.data = []
+        for e in range(mesh.n_elems):
+            n = int(mesh.n[e])
+            xl, _ = tables.lgl_nodes_weights(n)
+            xi, w, J, detJ, Jinv = sipg.volume_geometry(mesh, e)
+            Psi, _ = tables.basis3d(xl, xi)
+            self.data.append((Psi, w * detJ, coef(mesh.position_at(e, xi))))
+
+    def residual(self, u):
+        R = self.L @ u - self.F
+        off = self.mesh.dof_off
+        for e, (Psi, wd, c) in enumerate(self.data):
+            ug = Psi @ u[off[e]:off[e + 1]]
+            R[off[e]:off[e + 1]] -= Psi.T @ (wd * c * ug ** self.k)
+        return R
+
+    def jacobian_coef(self, u):
+        off = self.mesh.dof_off
+        return [-self.k * c * (Psi @ u[off[e]:off[e + 1]]) ** (self.k - 1)
+                for e, (Psi, wd, c) in enumerate(self.data)]

@@ -108,6 +108,11 @@ struct dg_ctx {
     // puncture data on the finest level volume points
     double* p_alpha = nullptr;
     double* p_beta = nullptr;
+    int nl_kind = 0;                // nonlinear problem for dg_newton_*: 0 none, 1 puncture, 2 power-law source
+    int nl_power = 0;
+    double* nl_coef = nullptr;      // power-law source coefficient at the finest volume GL points
+    double* nl_F = nullptr;         // power-law source: forcing vector (Dirichlet lift), n_dofs
+    bool nl_has_F = false;
     double* nw[4] = {};             // Newton work vectors (double, finest): R, du, Lu, S
     bool galerkin_ready = false;
     // CUDA graph of the V-cycle used inside dg_solve (captured once, replayed)

@@ -140,11 +140,13 @@ NlArgs nl_args(dg_ctx* c) {
     LevelDev& F = c->lv.back();
     NlArgs a{};
     a.n_elems = F.h.n_elems();
+    a.kind = c->nl_kind;
+    a.power = c->nl_power;
     a.p = F.p;
     a.dof_off = F.dof_off;
     a.vqp_off = F.vqp_off;
     a.wdetJ = F.wdetJ;
-    a.alpha = c->p_alpha;
+    a.alpha = c->nl_kind == kNlPower ? c->nl_coef : c->p_alpha;
     a.beta = c->p_beta;
     a.tab = c->tab64;
     a.n_vqp = F.h.vqp_off.back();
@@ -152,10 +154,12 @@ NlArgs nl_args(dg_ctx* c) {
     return a;
 }
 
-// R = L u - S(u) with the zeroth-order term off; optionally writes the Jacobian
-// coefficient into the finest c0.  Returns ||R||_2 in *rn (synchronises).
-int puncture_residual_impl(dg_ctx* c, const double* u, double* R, bool jac, double* rn) {
-    if (!c->p_alpha) return dgi_set_error(DG_ERR_INVALID, "call dg_puncture_setup first");
+// R = L u - S(u) (- F for the power-law source) with the zeroth-order term
+// off; optionally writes the Jacobian coefficient into the finest c0.
+// Returns ||R||_2 in *rn (synchronises).
+int nonlinear_residual_impl(dg_ctx* c, const double* u, double* R, bool jac, double* rn) {
+    if (c->nl_kind == kNlNone)
+        return dgi_set_error(DG_ERR_INVALID, "call dg_puncture_setup or dg_power_source_setup first");
     int rc = ensure_newton_work(c);
     if (rc) return rc;
     const bool was = c->lv.back().z_active;
@@ -165,7 +169,7 @@ int puncture_residual_impl(dg_ctx* c, const double* u, double* R, bool jac, doub
     LevelDev& F = c->lv.back();
     CK2(launch_nl(nl_args(c), u, c->nw[3], jac ? F.c0_64 : nullptr, jac ? F.c0_32 : nullptr, c->st));
     const long long n = F.h.n_dofs();
-    CK2(launch_sub(c->nw[2], c->nw[3], R, n, c->st));
+    CK2(launch_sub(c->nw[2], c->nw[3], c->nl_kind == kNlPower && c->nl_has_F ? c->nl_F : nullptr, R, n, c->st));
     c->launches += 2;
     if (!jac && was) set_zeroth_active(c, true);
     if (rn) {
@@ -254,22 +258,48 @@ int dg_puncture_setup(dg_ctx* c, const dg_puncture_params* prm) {
     }
     CK2(launch_puncture(F.vxyz, nv, P, c->p_alpha, c->p_beta, c->st));
     c->launches += 1;
+    c->nl_kind = kNlPuncture;
+    return DG_OK;
+}
+
+int dg_power_source_setup(dg_ctx* c, const double* coef_qp, int power, const double* F) {
+    if (!c || !coef_qp) return dgi_set_error(DG_ERR_INVALID, "NULL argument");
+    if (power < 1 || power > 9) return dgi_set_error(DG_ERR_INVALID, "power must be in 1..9");
+    LevelDev& L = c->lv.back();
+    const long long nv = L.h.vqp_off.back(), n = L.h.n_dofs();
+    if (!c->nl_coef) {
+        c->nl_coef = c->arena.alloc<double>(nv);
+        c->nl_F = c->arena.alloc<double>(n);
+        if (c->arena.failed) return dgi_set_error(DG_ERR_OOM, "device allocation failed (nonlinear source)");
+    }
+    CK2(cudaMemcpyAsync(c->nl_coef, coef_qp, sizeof(double) * nv, cudaMemcpyDeviceToDevice, c->st));
+    if (F) CK2(cudaMemcpyAsync(c->nl_F, F, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
+    c->nl_has_F = F != nullptr;
+    c->nl_power = power;
+    c->nl_kind = kNlPower;
     return DG_OK;
 }
 
 int dg_puncture_residual(dg_ctx* c, const double* u, double* R) {
     if (!c || !u || !R) return dgi_set_error(DG_ERR_INVALID, "NULL argument");
-    return puncture_residual_impl(c, u, R, false, nullptr);
+    if (c->nl_kind != kNlPuncture) return dgi_set_error(DG_ERR_INVALID, "call dg_puncture_setup first");
+    return nonlinear_residual_impl(c, u, R, false, nullptr);
+}
+
+int dg_nonlinear_residual(dg_ctx* c, const double* u, double* R) {
+    if (!c || !u || !R) return dgi_set_error(DG_ERR_INVALID, "NULL argument");
+    return nonlinear_residual_impl(c, u, R, false, nullptr);
 }
 
 int dg_newton_step(dg_ctx* c, double* u, const dg_solver_opts* o, dg_solve_stats* s, double* rn_out) {
     if (!c || !u) return dgi_set_error(DG_ERR_INVALID, "NULL argument");
-    if (!c->p_alpha) return dgi_set_error(DG_ERR_INVALID, "call dg_puncture_setup first");
+    if (c->nl_kind == kNlNone)
+        return dgi_set_error(DG_ERR_INVALID, "call dg_puncture_setup or dg_power_source_setup first");
     int rc = ensure_galerkin_structure(c);
     if (rc) return rc;
     if ((rc = ensure_newton_work(c))) return rc;   // c->nw[] must exist before it is passed on
     double rn = 0.0;
-    rc = puncture_residual_impl(c, u, c->nw[0], true, &rn);   // R(u_k); Jacobian coefficient into c0
+    rc = nonlinear_residual_impl(c, u, c->nw[0], true, &rn);   // R(u_k); Jacobian coefficient into c0
     if (rc) return rc;
     if (rn_out) *rn_out = rn;
     if ((rc = build_galerkin(c))) return rc;                    // J_R(u_k) on every level
@@ -289,12 +319,13 @@ int dg_newton_step(dg_ctx* c, double* u, const dg_solver_opts* o, dg_solve_stats
 int dg_newton_solve(dg_ctx* c, double* u, double tol, int maxn, const dg_solver_opts* o, int* steps,
                     double* rn_out) {
     if (!c || !u) return dgi_set_error(DG_ERR_INVALID, "NULL argument");
-    if (!c->p_alpha) return dgi_set_error(DG_ERR_INVALID, "call dg_puncture_setup first");
+    if (c->nl_kind == kNlNone)
+        return dgi_set_error(DG_ERR_INVALID, "call dg_puncture_setup or dg_power_source_setup first");
     int k = 0, rc = ensure_newton_work(c);   // c->nw[] must exist before it is passed on
     if (rc) return rc;
     double rn = 0.0;
     while (true) {
-        rc = puncture_residual_impl(c, u, c->nw[0], false, &rn);
+        rc = nonlinear_residual_impl(c, u, c->nw[0], false, &rn);
         if (rc) return rc;
         if (!(rn >= tol) || k >= maxn) break;
         dg_solve_stats st{};

@@ -13,6 +13,10 @@
 //   [P_i n_j + P_j n_i - (delta_ij - n_i n_j) P.n] (zero spin);
 //   beta = alpha^7 A_ij A_ij / 8.  Source s(u) = beta (1 + alpha (1 + u))^-7,
 //   Jacobian coefficient f(u) = 7 alpha beta (1 + alpha (1 + u))^-8.
+// * Power-law source (the constant-density star of Sec. III.C,
+//   Lap psi + 2 pi rho psi^5 = 0): s(u) = c u^k, f(u) = -k c u^(k-1), with c
+//   given at the GL points; the nonlinear term is evaluated at the GL points
+//   after interpolating u there, as the paper describes for that problem.
 #include "newton.h"
 
 namespace dg {
@@ -92,16 +96,26 @@ __global__ void nl_kernel(NlArgs a, const double* u, double* S, double* jac64, f
     }
     __syncthreads();
     for (int k = threadIdx.x; k < n3; k += blockDim.x) {
-        const double al = a.alpha[vo + k], be = a.beta[vo + k], wd = a.wdetJ[vo + k];
-        const double base = 1.0 + al * (1.0 + b1[k]);
-        const double b2 = base * base, b4 = b2 * b2, b8 = b4 * b4;
-        const double inv7 = base / b8;      // base^-7
-        if (jac64) {
-            const double jc = wd * 7.0 * al * be / b8;
-            jac64[vo + k] = jc;
-            jac32[vo + k] = (float)jc;
+        const double wd = a.wdetJ[vo + k];
+        double s, jc;
+        if (a.kind == kNlPower) {
+            const double c = a.alpha[vo + k], uq = b1[k];
+            double pk1 = 1.0;                   // u^(k-1)
+            for (int q = 1; q < a.power; ++q) pk1 *= uq;
+            s = c * pk1 * uq;
+            jc = -a.power * c * pk1;            // d(-s)/du: the source grows with u
+        } else {
+            const double al = a.alpha[vo + k], be = a.beta[vo + k];
+            const double base = 1.0 + al * (1.0 + b1[k]);
+            const double b2 = base * base, b4 = b2 * b2, b8 = b4 * b4;
+            s = be * base / b8;                 // beta base^-7
+            jc = 7.0 * al * be / b8;
         }
-        b0[k] = wd * be * inv7;
+        if (jac64) {
+            jac64[vo + k] = wd * jc;
+            jac32[vo + k] = (float)(wd * jc);
+        }
+        b0[k] = wd * s;
     }
     __syncthreads();
     // lift: three transposed passes
@@ -127,10 +141,10 @@ __global__ void nl_kernel(NlArgs a, const double* u, double* S, double* jac64, f
     }
 }
 
-// R = Lu - S
-__global__ void sub_kernel(const double* Lu, const double* S, double* R, long long n) {
+// R = Lu - S - F
+__global__ void sub_kernel(const double* Lu, const double* S, const double* F, double* R, long long n) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        R[i] = Lu[i] - S[i];
+        R[i] = Lu[i] - S[i] - (F ? F[i] : 0.0);
 }
 
 // O_H for every coarse element H of one level (block per H, loop over its finest descendants).
@@ -221,8 +235,8 @@ cudaError_t launch_nl(const NlArgs& a, const double* u, double* S, double* jac64
     return cudaGetLastError();
 }
 
-cudaError_t launch_sub(const double* Lu, const double* S, double* R, long long n, cudaStream_t st) {
-    sub_kernel<<<grid_for(n), 256, 0, st>>>(Lu, S, R, n);
+cudaError_t launch_sub(const double* Lu, const double* S, const double* F, double* R, long long n, cudaStream_t st) {
+    sub_kernel<<<grid_for(n), 256, 0, st>>>(Lu, S, F, R, n);
     return cudaGetLastError();
 }
 

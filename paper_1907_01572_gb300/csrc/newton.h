@@ -11,13 +11,17 @@ struct PunctureDev {
     double P[16][3];
 };
 
+enum NlKind { kNlNone = 0, kNlPuncture = 1, kNlPower = 2 };
+
 struct NlArgs {
     int n_elems;
+    int kind;                  // kNlPuncture: s = beta (1 + alpha (1 + u))^-7; kNlPower: s = coef u^power
+    int power;
     const int* p;
     const long long* dof_off;
     const long long* vqp_off;
     const double* wdetJ;
-    const double* alpha;
+    const double* alpha;       // puncture: alpha; power: coef
     const double* beta;
     const double* tab;
     long long n_vqp;   // bounds check
@@ -44,7 +48,8 @@ cudaError_t launch_puncture(const double* vxyz, long long n, const PunctureDev& 
                             cudaStream_t st);
 // S = I^T (w det J beta (1 + alpha (1 + u))^-7); jac (optional) = w det J 7 alpha beta (...)^-8
 cudaError_t launch_nl(const NlArgs& a, const double* u, double* S, double* jac64, float* jac32, cudaStream_t st);
-cudaError_t launch_sub(const double* Lu, const double* S, double* R, long long n, cudaStream_t st);
+// R = Lu - S - F (F may be NULL)
+cudaError_t launch_sub(const double* Lu, const double* S, const double* F, double* R, long long n, cudaStream_t st);
 cudaError_t launch_galerkin(const GalerkinArgs& g, const double* c0, double* O64, float* O32, cudaStream_t st);
 
 }  // namespace dg

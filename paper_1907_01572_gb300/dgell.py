@@ -91,6 +91,8 @@ _SIGS = {
     "dg_set_zeroth_order": ([_P, _P], ctypes.c_int),
     "dg_puncture_setup": ([_P, ctypes.POINTER(dg_puncture_params)], ctypes.c_int),
     "dg_puncture_residual": ([_P, _P, _P], ctypes.c_int),
+    "dg_power_source_setup": ([_P, _P, ctypes.c_int, _P], ctypes.c_int),
+    "dg_nonlinear_residual": ([_P, _P, _P], ctypes.c_int),
     "dg_newton_step": ([_P, _P, ctypes.POINTER(dg_solver_opts), ctypes.POINTER(dg_solve_stats), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "dg_newton_solve": ([_P, _P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(dg_solver_opts), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "dg_convert": ([_P, ctypes.c_int64, ctypes.c_int, _P, ctypes.c_int, _P], ctypes.c_int),
@@ -325,6 +327,13 @@ class Context:
         rn = ctypes.c_double(0.0)
         _check(lib().dg_newton_step(self.h, _ptr(u), ctypes.byref(o), ctypes.byref(s), ctypes.byref(rn)))
         return rn.value, {k: getattr(s, k) for k, _ in dg_solve_stats._fields_}
+
+    def power_source_setup(self, coef_qp, power, F=None):
+        _check(lib().dg_power_source_setup(self.h, _ptr(coef_qp), int(power), _ptr(F)))
+
+    def nonlinear_residual(self, u, R):
+        _check(lib().dg_nonlinear_residual(self.h, _ptr(u), _ptr(R)))
+        return R
 
     def newton_solve(self, u, tol_newton=1e-10, max_newton=20, **kw):
         """Alg. 1; kw are the linear solver's options (tol, max_iter, mg_prec, ...)."""

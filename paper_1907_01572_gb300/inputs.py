@@ -418,3 +418,58 @@ def puncture_sphere_mesh(punctures, level=2, a=2.0, r=10.0, r_out=20.0, p_base=4
         per.append(leaves)
         p += [p_fine if lf[0] > level else p_base for lf in leaves]
     return _block_mesh(blocks, per, p)
+
+
+# ---- constant-density star: Lap psi + 2 pi rho psi^5 = 0, psi -> 1 at infinity ----
+def constant_density_star(rho0=1e-3, r0=1.0):
+    """Closed-form solution of the constant-density star (density rho0 inside
+    r0): psi = C u_a(r) inside with u_a = (a r0)^(1/2) / (r^2 + (a r0)^2)^(1/2),
+    C = (2 pi rho0 / 3)^(-1/4), and psi = b / r + 1 outside, b = r0 (C u_a(r0)
+    - 1).  a follows from continuity of psi' at r0, which works out to
+    rho0 r0^2 = 3 a^10 / (2 pi (1 + a^2)^6) (the paper prints the power 3 of
+    (1 + a^2), with which psi' jumps at r0).  The right side rises up to
+    a = sqrt(5) and falls after it; the weak-field root a > sqrt(5) (psi -> 1
+    as rho0 -> 0, the solution Newton reaches from psi = 1) is taken.
+    Returns dict(a, b, C, psi, rho, coef) with psi, rho and coef = 2 pi rho
+    callables on points (P, 3)."""
+    target = rho0 * r0 * r0 * 2.0 * np.pi / 3.0
+    lo, hi = np.sqrt(5.0), 1e8
+    for _ in range(300):
+        mid = np.sqrt(lo * hi)
+        if mid ** 10 / (1.0 + mid * mid) ** 6 > target:
+            lo = mid
+        else:
+            hi = mid
+    a = np.sqrt(lo * hi)
+    C = (2.0 * np.pi * rho0 / 3.0) ** -0.25
+    ua = lambda r: np.sqrt(a * r0) / np.sqrt(r * r + (a * r0) ** 2)
+    b = r0 * (C * ua(r0) - 1.0)
+
+    def psi(x):
+        r = np.linalg.norm(np.asarray(x, dtype=np.float64).reshape(-1, 3), axis=1)
+        return np.where(r <= r0, C * ua(r), b / np.maximum(r, 1e-300) + 1.0)
+
+    def rho(x):
+        r = np.linalg.norm(np.asarray(x, dtype=np.float64).reshape(-1, 3), axis=1)
+        return np.where(r <= r0, rho0, 0.0)
+
+    return dict(a=a, b=b, C=C, psi=psi, rho=rho, coef=lambda x: 2.0 * np.pi * rho(x))
+
+
+def const_star_mesh(R=8.0, level=2, refine=2, p=4, r0=1.0):
+    """Box [-R, R]^3 (the paper's boundary at 8 r0), uniform level `level`,
+    cells cut by the star surface r = r0 refined `refine` times (2:1
+    balanced); degree p everywhere."""
+    lo, hi = (-R, -R, -R), (R, R, R)
+    leaves = uniform_leaves(level)
+
+    def cut(lf):
+        a, b = _cell_bounds(lf, lo, hi)
+        dmin, dmax = _dist_range(a, b)
+        return dmin <= r0 <= dmax
+
+    for _ in range(refine):
+        leaves = balance_2to1(refine_(leaves, cut))
+    leaves = morton_sort(leaves)
+    return dict(lo=lo, hi=hi, leaves=np.array(leaves, dtype=np.int32), p=np.full(len(leaves), p, dtype=np.int32),
+                warp=None)

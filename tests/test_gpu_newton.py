@@ -142,3 +142,48 @@ def test_newton_on_cubed_sphere_matches_oracle():
         assert rn < 1e-10 * hist[0] and steps <= ko + 2, (steps, rn, hist)
         assert rel_l2(ug.cpu().numpy(), uo) < 1e-8
     ctx.close()
+
+
+def test_constant_density_star_newton_matches_oracle():
+    """Constant-density star (Lap psi + 2 pi rho psi^5 = 0, Dirichlet data from
+    the closed form at 8 r0) through the power-law-source Newton path:
+    residual parity, Newton from psi = 1 with FP64 and FP32 V-cycles against
+    the oracle's Newton, and the same L2 error against the closed form."""
+    import scipy.sparse as sp
+    import torch
+    from paper_1907_01572_gb300 import dgell
+    st = inputs.constant_density_star()
+    desc = inputs.const_star_mesh(level=2, refine=1, p=3)
+    m = Mesh(desc["lo"], desc["hi"], desc["leaves"], desc["p"])
+    Fo = sipg.rhs(m, lambda x: np.zeros(len(x)), st["psi"], 10.0)
+    prob = puncture.PowerSourceProblem(m, st["coef"], 5, Fo)
+
+    def ls(coef, rhs):
+        M = sp.block_diag([sp.csr_matrix(sipg.element_mass(m, e, coef[e])) for e in range(m.n_elems)], format="csr")
+        x, info = spla.cg(prob.L + M, rhs, rtol=1e-14, maxiter=20000)
+        return x
+
+    uo, ko, hist = puncture.newton(prob, np.ones(m.n_dofs), ls, tol=1e-11 * np.linalg.norm(Fo))
+    ctx = dgell.Context(desc)
+    xyz, bxyz = ctx.quadrature_points()
+    F = torch.empty(m.n_dofs, dtype=torch.float64, device="cuda")
+    ctx.rhs(None, torch.tensor(st["psi"](bxyz.T.cpu().numpy()), device="cuda"), F)
+    assert rel_l2(F.cpu().numpy(), Fo) < 1e-12
+    ctx.power_source_setup(torch.tensor(st["coef"](xyz.T.cpu().numpy()), device="cuda"), 5, F)
+    u = 1.0 + 0.01 * inputs.random_vector(m.n_dofs, seed=8)
+    R = torch.empty_like(F)
+    ctx.nonlinear_residual(torch.tensor(u, device="cuda"), R)
+    assert rel_l2(R.cpu().numpy(), prob.residual(u)) < 1e-12
+    err_o = sipg.l2_error(m, uo, st["psi"], extra=2)
+    for prec in (dgell.DG_FP64, dgell.DG_FP32):
+        ug = torch.ones(m.n_dofs, dtype=torch.float64, device="cuda")
+        steps, rn = ctx.newton_solve(ug, tol_newton=1e-10 * hist[0], max_newton=10, mg_prec=prec, tol=1e-11,
+                                     max_iter=300)
+        assert rn < 1e-10 * hist[0] and steps <= ko + 1, (steps, rn, hist)
+        assert rel_l2(ug.cpu().numpy(), uo) < 1e-8
+        err = sipg.l2_error(m, ug.cpu().numpy(), st["psi"], extra=2)
+        assert abs(err - err_o) < 0.01 * err_o
+    # the puncture-only residual call refuses while the power-law source is set
+    with pytest.raises(dgell.DgError):
+        ctx.puncture_residual(torch.tensor(u, device="cuda"), R)
+    ctx.close()
