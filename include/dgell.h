@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define DGELL_VERSION 109
+#define DGELL_VERSION 110
 
 enum {
     DG_OK = 0,

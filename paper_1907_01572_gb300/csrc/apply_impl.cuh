@@ -368,8 +368,12 @@ struct Layout {
     static constexpr int TFACE = 2 * N2 + 3 * kQ * N;                 // trace kernel face scratch
     static constexpr int TWARP = NR + TFACE;
     static constexpr int EFACE = 4 * kQ * kQ + 3 * kQ * N;            // element kernel face scratch
-    static constexpr bool ALIAS = 4 * NR >= EFACE;                    // reuses the volume scratch
-    static constexpr int EWARP = ALIAS ? 6 * NR : 6 * NR + EFACE;
+    // UALIAS: the input buffer, dead after the first volume pass, holds the
+    // z-gradient, and A, B, G1 (3 arrays) hold the face scratch; else six
+    // arrays with the face scratch in A..G3.
+    static constexpr bool UALIAS = 3 * NR >= EFACE;
+    static constexpr bool ALIAS = UALIAS || 4 * NR >= EFACE;          // face scratch reuses the volume scratch
+    static constexpr int EWARP = UALIAS ? 5 * NR : (ALIAS ? 6 * NR : 6 * NR + EFACE);
 };
 
 // Values ahead of the per-warp scratch: FP32 mortar tables (staged) and the
@@ -549,7 +553,7 @@ __device__ __forceinline__ void element_body(const LevelView<T>& L, const int* _
     T* A = Y + NR;
     T* B = A + NR;
     T* G1 = B + NR;
-    T* G3 = G1 + NR;
+    T* G3 = Ly::UALIAS ? U : G1 + NR;
     T* G2 = Y;  // the y-gradient lives in Y until the backward passes
     T* F = Ly::ALIAS ? A : G3 + NR;
     const bool mass = L.c0 != nullptr;
@@ -604,7 +608,8 @@ __device__ __forceinline__ void element_body(const LevelView<T>& L, const int* _
             const T* Oe = L.Ob + L.Ob_off[e];
             for (int k = lane; k < N3; k += 32) {
                 T s = 0;
-                for (int j = 0; j < N3; ++j) s += Oe[(long long)j * N3 + k] * U[j];
+                for (int j = 0; j < N3; ++j)   // u from the input vector when its buffer was reused
+                    s += Oe[(long long)j * N3 + k] * (Ly::UALIAS ? ld<T>(x + dofo + j) : U[j]);
                 Y[k] += s;
             }
             __syncwarp();
