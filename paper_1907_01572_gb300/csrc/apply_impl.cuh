@@ -816,10 +816,14 @@ __global__ void element_cta(LevelView<T> L, FusedBuckets fb, const TX* __restric
     DG_BODY_SWITCH(fb.n[b], (element_body_cta<NN, T, TX>(L, e, x, y)))
 }
 
-inline int& sm_count() {
-    static int v = 0;
-    return v;
-}
+// Launch shape of a per-bucket kernel, found once per template instance.  The
+// statics below are initialised by the first caller (C++ guarantees that
+// this is thread-safe), as the serving loop applies from several threads.
+struct LaunchShape {
+    cudaError_t err;
+    int W, per_sm;
+    size_t smem;
+};
 
 // Warps per CTA and resident CTAs per SM: the configuration with the most
 // resident warps (up to 32 per CTA) that shared memory and registers allow.
@@ -848,26 +852,27 @@ cudaError_t pick_warps(K kernel, size_t table_bytes, size_t warp_bytes, int& W, 
 }
 
 inline int grid_cap() {
-    int& g = sm_count();
-    if (g == 0) {
-        int dev = 0;
+    static const int g = [] {
+        int dev = 0, v = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g, cudaDevAttrMultiProcessorCount, dev);
-        if (g <= 0) g = 152;
-    }
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 152;
+    }();
     return g;
 }
 
 template <int N, typename T, typename TX, bool OR>
 cudaError_t launch_trace(const LevelView<T>& L, const BucketInfo& b, const TX* x, cudaStream_t st) {
     using Ly = Layout<N>;
-    static int W = 0, per_sm = 1;
-    static size_t smem = 0;
-    if (W == 0) {
+    static const LaunchShape shp = [&] {   // the mortar tables have the same size in every context
+        LaunchShape r{};
         const size_t table_bytes = table_vals<N>(sizeof(T) == 4 ? L.ft.total : 0) * sizeof(T);
-        cudaError_t err = pick_warps(trace_kernel<N, T, TX, OR>, table_bytes, Ly::TWARP * sizeof(T), W, smem, per_sm);
-        if (err != cudaSuccess) return err;
-    }
+        r.err = pick_warps(trace_kernel<N, T, TX, OR>, table_bytes, Ly::TWARP * sizeof(T), r.W, r.smem, r.per_sm);
+        return r;
+    }();
+    if (shp.err != cudaSuccess) return shp.err;
+    const int W = shp.W, per_sm = shp.per_sm;
+    const size_t smem = shp.smem;
     int grid = (b.count + W - 1) / W;
     if (grid > grid_cap() * per_sm) grid = grid_cap() * per_sm;
     trace_kernel<N, T, TX, OR><<<grid, W * 32, smem, st>>>(L, b.elems, b.count, x, L.mt);
@@ -877,13 +882,15 @@ cudaError_t launch_trace(const LevelView<T>& L, const BucketInfo& b, const TX* x
 template <int N, typename T, typename TX, bool OR>
 cudaError_t launch_element(const LevelView<T>& L, const BucketInfo& b, const TX* x, T* y, cudaStream_t st) {
     using Ly = Layout<N>;
-    static int W = 0, per_sm = 1;
-    static size_t smem = 0;
-    if (W == 0) {
+    static const LaunchShape shp = [&] {   // the mortar tables have the same size in every context
+        LaunchShape r{};
         const size_t table_bytes = table_vals<N>(sizeof(T) == 4 ? L.ft.total : 0) * sizeof(T);
-        cudaError_t err = pick_warps(element_kernel<N, T, TX, OR>, table_bytes, Ly::EWARP * sizeof(T), W, smem, per_sm);
-        if (err != cudaSuccess) return err;
-    }
+        r.err = pick_warps(element_kernel<N, T, TX, OR>, table_bytes, Ly::EWARP * sizeof(T), r.W, r.smem, r.per_sm);
+        return r;
+    }();
+    if (shp.err != cudaSuccess) return shp.err;
+    const int W = shp.W, per_sm = shp.per_sm;
+    const size_t smem = shp.smem;
     int grid = (b.count + W - 1) / W;
     if (grid > grid_cap() * per_sm) grid = grid_cap() * per_sm;
     element_kernel<N, T, TX, OR><<<grid, W * 32, smem, st>>>(L, b.elems, b.count, x, y);
@@ -942,14 +949,12 @@ cudaError_t launch_fused_warp(const LevelView<T>& L, const BucketInfo* buckets, 
         ++fb.nb;
     }
     fb.cta_start[fb.nb] = ctas;
-    static bool attr = false;
-    if (!attr) {
+    static const cudaError_t attr = [&] {
         cudaError_t e1 = cudaFuncSetAttribute(trace_fused<T, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
         cudaError_t e2 = cudaFuncSetAttribute(element_fused<T, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
-        if (e1 != cudaSuccess) return e1;
-        if (e2 != cudaSuccess) return e2;
-        attr = true;
-    }
+        return e1 != cudaSuccess ? e1 : e2;
+    }();
+    if (attr != cudaSuccess) return attr;
     trace_fused<T, TX><<<ctas, W * 32, smem_t, st>>>(L, fb, x, L.mt);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
@@ -986,14 +991,12 @@ cudaError_t launch_fused_cta(const LevelView<T>& L, const BucketInfo* buckets, c
     fb.cta_start[fb.nb] = ctas;
     if (ctas == 0) return cudaSuccess;
     if (smem_e > cap || smem_t > cap) return cudaErrorInvalidConfiguration;
-    static bool attr = false;
-    if (!attr) {
+    static const cudaError_t attr = [&] {
         cudaError_t e1 = cudaFuncSetAttribute(trace_cta<T, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
         cudaError_t e2 = cudaFuncSetAttribute(element_cta<T, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
-        if (e1 != cudaSuccess) return e1;
-        if (e2 != cudaSuccess) return e2;
-        attr = true;
-    }
+        return e1 != cudaSuccess ? e1 : e2;
+    }();
+    if (attr != cudaSuccess) return attr;
     trace_cta<T, TX><<<ctas, kCtaWarps * 32, smem_t, st>>>(L, fb, x, L.mt);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;

@@ -46,12 +46,11 @@ void plan_cache_put(unsigned long long key, int plan) {
 }
 
 bool debug_sync() {
-    static int v = -1;
-    if (v < 0) {
+    static const bool v = [] {   // read once (thread-safe static initialisation)
         const char* e = std::getenv("DGELL_DEBUG_SYNC");
-        v = (e && e[0] == '1') ? 1 : 0;
-    }
-    return v == 1;
+        return e && e[0] == '1';
+    }();
+    return v;
 }
 
 }  // namespace dg

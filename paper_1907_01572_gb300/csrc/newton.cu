@@ -242,12 +242,9 @@ cudaError_t launch_sub(const double* Lu, const double* S, const double* F, doubl
 
 cudaError_t launch_galerkin(const GalerkinArgs& g, const double* c0, double* O64, float* O32, cudaStream_t st) {
     const size_t smem = sizeof(double) * (kMaxN * kMaxN * kMaxN * kMaxN + kMaxN * kMaxN * kMaxN);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(galerkin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static const cudaError_t attr =   // once per process, thread-safe initialisation
+        cudaFuncSetAttribute(galerkin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr != cudaSuccess) return attr;
     galerkin_kernel<<<g.n_coarse, 256, smem, st>>>(g, c0, O64, O32);
     return cudaGetLastError();
 }
