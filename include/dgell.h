@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define DGELL_VERSION 110
+#define DGELL_VERSION 111
 
 enum {
     DG_OK = 0,
@@ -220,6 +220,15 @@ int dg_smooth_static(dg_ctx* ctx, int level, int prec, const void* b, void* x,
 typedef struct {
     dg_cheb_opts cheb;
     int coarse;        /* 0: smoother on level 0 (paper), 1: dense Cholesky */
+    int smoother;      /* 0: Chebyshev with CG eigenvalue bound (Alg. 4, 5);
+                          1: Schwarz smoother (Alg. 6) with element subdomains and no overlap:
+                          n_schwarz cycles of r = b - J x, element-local CG on the element
+                          diagonal blocks J_ee dx_e = r_e (all elements at once, to local_tol
+                          or local_iters steps), x += schwarz_omega dx */
+    int n_schwarz;     /* <= 0 -> 3 (the paper's typical N_s) */
+    int local_iters;   /* <= 0 -> 20 */
+    double local_tol;  /* relative; <= 0 -> 1e-3 (the paper's local tolerance) */
+    double schwarz_omega;  /* damping; <= 0 -> 0.7 (without overlap the paper's weights are 1) */
 } dg_mg_opts;
 
 int dg_vcycle(dg_ctx* ctx, int prec, const void* f, void* v, const dg_mg_opts* opts);

@@ -293,10 +293,14 @@ __device__ __forceinline__ void lift_slot(const LevelView<T>& L, const SlotInfo<
         for (int k = lane; k < Q2; k += 32) {
             const int kA = OR ? toA(k % Q, k / Q) : k;
             const T wS = wSp[kA];
-            const T uA = m[kA], dA = m[Q2 + kA];
+            T uA = m[kA], dA = m[Q2 + kA];
             T jmp, avg, bc;
             if (interior) {
-                const T uB = m[2 * Q2 + kA], dB = m[3 * Q2 + kA];
+                T uB = m[2 * Q2 + kA], dB = m[3 * Q2 + kA];
+                if (L.bdiag) {   // element diagonal block: the other side's trace is zero
+                    if (s.side == 0) uB = dB = T(0);
+                    else uA = dA = T(0);
+                }
                 jmp = sgn * (uA - uB);
                 avg = T(0.5) * sgn * (dA + dB);
                 bc = T(-0.5) * wS * jmp;

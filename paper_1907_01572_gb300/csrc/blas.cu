@@ -519,4 +519,111 @@ template cudaError_t dense_matvec_t<double>(const double*, const double*, double
 template cudaError_t dense_matvec_t<float>(const float*, const float*, float*, int, cudaStream_t);
 template cudaError_t dense_matvec<float>(const double*, const float*, float*, int, cudaStream_t);
 
+
+// ---- element-local CG (Schwarz smoother) ------------------------------------------
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {   // fixed butterfly order
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T>
+__global__ void elem_cg_init_kernel(const T* r, T* p, T* dx, const long long* dof_off, int ne, double* es) {
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int e = blockIdx.x * wpb + (threadIdx.x >> 5); e < ne; e += gridDim.x * wpb) {
+        const long long a = dof_off[e], b = dof_off[e + 1];
+        double s = 0.0;
+        for (long long i = a + lane; i < b; i += 32) {
+            const T v = r[i];
+            p[i] = v;
+            dx[i] = T(0);
+            s += (double)v * (double)v;
+        }
+        s = warp_sum(s);
+        if (lane == 0) {
+            es[3 * e] = s;
+            es[3 * e + 1] = 0.0;
+            es[3 * e + 2] = s;
+        }
+    }
+}
+
+template <typename T>
+__global__ void elem_cg_alpha_kernel(const T* p, const T* Dp, const long long* dof_off, int ne, double* es,
+                                     double tol2) {
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int e = blockIdx.x * wpb + (threadIdx.x >> 5); e < ne; e += gridDim.x * wpb) {
+        const long long a = dof_off[e], b = dof_off[e + 1];
+        double s = 0.0;
+        for (long long i = a + lane; i < b; i += 32) s += (double)p[i] * (double)Dp[i];
+        s = warp_sum(s);
+        if (lane == 0) {
+            const double rr = es[3 * e];
+            es[3 * e + 1] = (rr > tol2 * es[3 * e + 2] && s > 0.0 && isfinite(s)) ? rr / s : 0.0;
+        }
+    }
+}
+
+template <typename T>
+__global__ void elem_cg_update_kernel(T* dx, T* r, T* p, const T* Dp, const long long* dof_off, int ne,
+                                      double* es) {
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int e = blockIdx.x * wpb + (threadIdx.x >> 5); e < ne; e += gridDim.x * wpb) {
+        const double alpha = es[3 * e + 1];
+        if (alpha == 0.0) continue;   // warp-uniform: this element's local solve has stopped
+        const long long a = dof_off[e], b = dof_off[e + 1];
+        const T al = (T)alpha;
+        double s = 0.0;
+        for (long long i = a + lane; i < b; i += 32) {
+            dx[i] += al * p[i];
+            const T v = r[i] - al * Dp[i];
+            r[i] = v;
+            s += (double)v * (double)v;
+        }
+        s = warp_sum(s);
+        const double rr = es[3 * e];
+        const T beta = (T)(rr > 0.0 ? s / rr : 0.0);
+        for (long long i = a + lane; i < b; i += 32) p[i] = r[i] + beta * p[i];
+        __syncwarp();
+        if (lane == 0) es[3 * e] = s;
+    }
+}
+
+inline int elem_grid(int ne) {
+    const int g = (ne + 7) / 8;
+    return g < 1 ? 1 : (g > 4 * kRedBlocks ? 4 * kRedBlocks : g);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t elem_cg_init(const T* r, T* p, T* dx, const long long* dof_off, int ne, double* es, cudaStream_t st) {
+    elem_cg_init_kernel<T><<<elem_grid(ne), 256, 0, st>>>(r, p, dx, dof_off, ne, es);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t elem_cg_alpha(const T* p, const T* Dp, const long long* dof_off, int ne, double* es, double tol2,
+                          cudaStream_t st) {
+    elem_cg_alpha_kernel<T><<<elem_grid(ne), 256, 0, st>>>(p, Dp, dof_off, ne, es, tol2);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t elem_cg_update(T* dx, T* r, T* p, const T* Dp, const long long* dof_off, int ne, double* es,
+                           cudaStream_t st) {
+    elem_cg_update_kernel<T><<<elem_grid(ne), 256, 0, st>>>(dx, r, p, Dp, dof_off, ne, es);
+    return cudaGetLastError();
+}
+template cudaError_t elem_cg_init<float>(const float*, float*, float*, const long long*, int, double*, cudaStream_t);
+template cudaError_t elem_cg_init<double>(const double*, double*, double*, const long long*, int, double*,
+                                          cudaStream_t);
+template cudaError_t elem_cg_alpha<float>(const float*, const float*, const long long*, int, double*, double,
+                                          cudaStream_t);
+template cudaError_t elem_cg_alpha<double>(const double*, const double*, const long long*, int, double*, double,
+                                           cudaStream_t);
+template cudaError_t elem_cg_update<float>(float*, float*, float*, const float*, const long long*, int, double*,
+                                           cudaStream_t);
+template cudaError_t elem_cg_update<double>(double*, double*, double*, const double*, const long long*, int,
+                                            double*, cudaStream_t);
+
 }  // namespace dg

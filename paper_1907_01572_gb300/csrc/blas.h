@@ -65,6 +65,21 @@ cudaError_t fcg_dq(const FcgState* f, double* d, double* q, const double* v, con
 cudaError_t fcg_update(const FcgState* f, double* u, double* r, const double* d, const double* q, long long n,
                        Red red, cudaStream_t st);
 
+// Element-local CG on a block-diagonal system (the Schwarz smoother's local
+// solves, all elements at once), warp per element, per-element scalars in
+// es[3 * e + {0, 1, 2}] = (r.r, alpha, initial r.r):
+//   init:   dx = 0, p = r, es = (r.r, 0, r.r)
+//   alpha:  alpha_e = r.r / p.Dp, or 0 once r.r <= tol2 * (initial r.r) or p.Dp <= 0
+//   update: dx += alpha p, r -= alpha Dp, p = r + (r.r_new / r.r) p
+template <typename T>
+cudaError_t elem_cg_init(const T* r, T* p, T* dx, const long long* dof_off, int ne, double* es, cudaStream_t st);
+template <typename T>
+cudaError_t elem_cg_alpha(const T* p, const T* Dp, const long long* dof_off, int ne, double* es, double tol2,
+                          cudaStream_t st);
+template <typename T>
+cudaError_t elem_cg_update(T* dx, T* r, T* p, const T* Dp, const long long* dof_off, int ne, double* es,
+                           cudaStream_t st);
+
 template <typename T>
 cudaError_t axpby(T a, const T* x, T b, T* y, long long n, cudaStream_t st);   // y = a x + b y
 template <typename T>

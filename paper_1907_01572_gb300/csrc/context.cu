@@ -280,6 +280,56 @@ int smooth_t(dg_ctx* c, int l, const T* b, T* x, const dg_cheb_opts* o) {
     return DG_OK;
 }
 
+// y = blockdiag(J_ee) x: the apply with each mortar's other-side trace taken as 0.
+template <typename T>
+int apply_bdiag_t(dg_ctx* c, int l, const T* x, T* y) {
+    int launches = 0;
+    LevelView<T> v = view<T>(c, l);
+    v.bdiag = 1;
+    CK(launch_apply<T>(v, c->lv[l].buckets, x, y, c->st, &launches, &c->lv[l].plan[sizeof(T) == 8 ? 0 : 1],
+                       &c->as));
+    c->launches += launches;
+    return DG_OK;
+}
+
+// Alg. 6 (Schwarz smoother) with element subdomains and no overlap: cycles of
+// r = b - J x, element-local CG on J_ee dx_e = r_e for all elements at once
+// (relative tolerance local_tol, at most local_iters steps), x += omega dx.
+template <typename T>
+int smooth_schwarz_t(dg_ctx* c, int l, const T* b, T* x, const dg_mg_opts* o) {
+    int rc = ensure_work<T>(c, l);
+    if (rc) return rc;
+    if ((rc = ensure_dense(c, l))) return rc;
+    LevelDev& L = c->lv[l];
+    const int ne = L.h.n_elems();
+    if (!L.schwarz_es) {
+        L.schwarz_es = c->arena.alloc<double>(3 * (size_t)ne);
+        if (c->arena.failed) return fail(DG_ERR_OOM, "device allocation failed (Schwarz smoother)");
+    }
+    const int ns = o->n_schwarz > 0 ? o->n_schwarz : 3;
+    const int K = o->local_iters > 0 ? o->local_iters : 20;
+    const double tol = o->local_tol > 0 ? o->local_tol : 1e-3;
+    const double om = o->schwarz_omega > 0 ? o->schwarz_omega : 0.7;
+    Work<T>& W = work_of<T>(L);
+    const long long n = L.h.n_dofs();
+    cudaStream_t st = c->st;
+    for (int s = 0; s < ns; ++s) {
+        if ((rc = solver_apply<T>(c, l, x, W.Ap))) return rc;
+        CK(sub3<T>(b, W.Ap, W.r, n, st));
+        CK(elem_cg_init<T>(W.r, W.p, W.t, L.dof_off, ne, L.schwarz_es, st));
+        c->launches += 2;
+        for (int k = 0; k < K; ++k) {
+            if ((rc = apply_bdiag_t<T>(c, l, W.p, W.Ap))) return rc;
+            CK(elem_cg_alpha<T>(W.p, W.Ap, L.dof_off, ne, L.schwarz_es, tol * tol, st));
+            CK(elem_cg_update<T>(W.t, W.r, W.p, W.Ap, L.dof_off, ne, L.schwarz_es, st));
+            c->launches += 2;
+        }
+        CK(axpby<T>((T)om, W.t, (T)1, x, n, st));
+        c->launches += 1;
+    }
+    return DG_OK;
+}
+
 template <typename T>
 TransferView<T> tview(dg_ctx* c, int lc) {
     LevelDev& H = c->lv[lc];
@@ -370,13 +420,16 @@ int vcycle_t(dg_ctx* c, const T* f, T* v, const dg_mg_opts* o) {
         if ((rc = ensure_work<T>(c, l))) return rc;
     if (o && o->coarse == 1 && (rc = ensure_coarse_inverse(c))) return rc;
     const dg_cheb_opts* co = o ? &o->cheb : nullptr;
+    auto smooth = [&](int l, const T* b, T* x) {
+        return (o && o->smoother == 1) ? smooth_schwarz_t<T>(c, l, b, x, o) : smooth_t<T>(c, l, b, x, co);
+    };
     auto F = [&](int l) -> const T* { return l == Lt ? f : work_of<T>(c->lv[l]).f; };
     auto V = [&](int l) -> T* { return l == Lt ? v : work_of<T>(c->lv[l]).v; };
     for (int l = Lt; l >= 1; --l) {
         const long long n = c->lv[l].h.n_dofs();
         Work<T>& W = work_of<T>(c->lv[l]);
         CK(cudaMemsetAsync(V(l), 0, n * sizeof(T), st));
-        if ((rc = smooth_t<T>(c, l, F(l), V(l), co))) return rc;
+        if ((rc = smooth(l, F(l), V(l)))) return rc;
         if ((rc = solver_apply<T>(c, l, V(l), W.t))) return rc;
         CK(sub3<T>(F(l), W.t, W.r, n, st));
         CK(launch_restrict<T>(tview<T>(c, l - 1), W.r, work_of<T>(c->lv[l - 1]).f, st));
@@ -389,13 +442,13 @@ int vcycle_t(dg_ctx* c, const T* f, T* v, const dg_mg_opts* o) {
             c->launches += 1;
         } else {
             CK(cudaMemsetAsync(V(0), 0, n0 * sizeof(T), st));
-            if ((rc = smooth_t<T>(c, 0, F(0), V(0), co))) return rc;
+            if ((rc = smooth(0, F(0), V(0)))) return rc;
         }
     }
     for (int l = 1; l <= Lt; ++l) {
         CK(launch_prolong_add<T>(tview<T>(c, l - 1), V(l - 1), V(l), st));
         c->launches += 1;
-        if ((rc = smooth_t<T>(c, l, F(l), V(l), co))) return rc;
+        if ((rc = smooth(l, F(l), V(l)))) return rc;
     }
     return DG_OK;
 }
@@ -404,7 +457,9 @@ bool same_opts(const dg_mg_opts& a, const dg_mg_opts* b) {
     const dg_mg_opts z{};
     const dg_mg_opts& bb = b ? *b : z;
     return a.coarse == bb.coarse && a.cheb.n_eigs == bb.cheb.n_eigs && a.cheb.n_cheb == bb.cheb.n_cheb &&
-           a.cheb.Lambda == bb.cheb.Lambda && a.cheb.lam_scale == bb.cheb.lam_scale;
+           a.cheb.Lambda == bb.cheb.Lambda && a.cheb.lam_scale == bb.cheb.lam_scale && a.smoother == bb.smoother &&
+           a.n_schwarz == bb.n_schwarz && a.local_iters == bb.local_iters && a.local_tol == bb.local_tol &&
+           a.schwarz_omega == bb.schwarz_omega;
 }
 
 // The V-cycle of one FCG iteration (FP64: r -> v; FP32: fcg32[0] -> fcg32[1]).

@@ -49,6 +49,7 @@ struct LevelDev {
     LevelHost h;
     int *leaves = nullptr, *p = nullptr, *block = nullptr;
     int oriented = 0;                 // some mortar has a turned side B (block interfaces)
+    double* schwarz_es = nullptr;     // element-local CG scalars of the Schwarz smoother (3 per element)
     long long *dof_off = nullptr, *vqp_off = nullptr;
     Mortar* mortars = nullptr;
     int *slot_off = nullptr, *slot_mortar = nullptr;

@@ -137,6 +137,7 @@ struct LevelView {         // passed by value to kernels
     FaceTabs ft;
     long long ob_total;    // entries of Ob (bounds check)
     int oriented;          // some mortar of the level has a turned side B (Mortar::orient != 0)
+    int bdiag;             // apply only the element diagonal blocks (the neighbour's trace taken as 0)
     int* chk;              // self-check flag
     T* mt;                 // mortar trace buffer: 4 * n_mortar_pts ([u_A, dn_A, u_B, dn_B] per mortar)
 };

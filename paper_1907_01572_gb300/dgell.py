@@ -54,7 +54,9 @@ class dg_cheb_opts(ctypes.Structure):
 
 
 class dg_mg_opts(ctypes.Structure):
-    _fields_ = [("cheb", dg_cheb_opts), ("coarse", ctypes.c_int)]
+    _fields_ = [("cheb", dg_cheb_opts), ("coarse", ctypes.c_int), ("smoother", ctypes.c_int),
+                ("n_schwarz", ctypes.c_int), ("local_iters", ctypes.c_int), ("local_tol", ctypes.c_double),
+                ("schwarz_omega", ctypes.c_double)]
 
 
 class dg_solver_opts(ctypes.Structure):
@@ -207,8 +209,10 @@ def cheb_opts(n_eigs=15, n_cheb=15, Lambda=20.0, lam_scale=1.0):
     return dg_cheb_opts(n_eigs, n_cheb, Lambda, lam_scale)
 
 
-def mg_opts(n_eigs=15, n_cheb=15, Lambda=20.0, coarse=0, lam_scale=1.0):
-    return dg_mg_opts(cheb_opts(n_eigs, n_cheb, Lambda, lam_scale), coarse)
+def mg_opts(n_eigs=15, n_cheb=15, Lambda=20.0, coarse=0, lam_scale=1.0, smoother=0, n_schwarz=3, local_iters=20,
+            local_tol=1e-3, schwarz_omega=0.7):
+    return dg_mg_opts(cheb_opts(n_eigs, n_cheb, Lambda, lam_scale), coarse, smoother, n_schwarz, local_iters,
+                      local_tol, schwarz_omega)
 
 
 def solver_opts(tol=1e-10, max_iter=100, mg_prec=DG_FP64, use_mg=1, graph_mode=0, **mg):
