@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define DGELL_VERSION 111
+#define DGELL_VERSION 112
 
 enum {
     DG_OK = 0,

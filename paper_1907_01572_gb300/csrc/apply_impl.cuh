@@ -268,7 +268,7 @@ __device__ __forceinline__ void trace_slot(const LevelView<T>& L, const SlotInfo
 // Flux at the mortar points and lift into Y for one mortar of the element.  Per
 // mortar point: surface weight wSp, this side's c (three Q^2 blocks at co) and
 // the trace buffer entries m = [u_A, dn_A, u_B, dn_B] (Q^2 each).
-template <int N, int Q, typename T, bool OR = true>
+template <int N, int Q, typename T, bool OR = true, int BDM = 2>
 __device__ __forceinline__ void lift_slot(const LevelView<T>& L, const SlotInfo<T>& s, bool interior, T sig,
                                           T* __restrict__ Y, const T* __restrict__ sDL, const T* __restrict__ sFT,
                                           T* F, const T* __restrict__ wSp, const T* __restrict__ co,
@@ -297,7 +297,7 @@ __device__ __forceinline__ void lift_slot(const LevelView<T>& L, const SlotInfo<
             T jmp, avg, bc;
             if (interior) {
                 T uB = m[2 * Q2 + kA], dB = m[3 * Q2 + kA];
-                if (L.bdiag) {   // element diagonal block: the other side's trace is zero
+                if (BDM == 1 || (BDM == 2 && L.bdiag)) {   // element diagonal block: the other side's trace is zero
                     if (s.side == 0) uB = dB = T(0);
                     else uA = dA = T(0);
                 }
@@ -543,7 +543,8 @@ __global__ void trace_kernel(LevelView<T> L, const int* __restrict__ bucket, int
     trace_body<N, T, TX, OR>(L, bucket, count, x, mt, blockIdx.x, gridDim.x);
 }
 
-template <int N, typename T, typename TX, bool OR = true>
+// BDM: element diagonal blocks only -- 0 never, 1 always, 2 as L.bdiag says.
+template <int N, typename T, typename TX, bool OR = true, int BDM = 2>
 __device__ __forceinline__ void element_body(const LevelView<T>& L, const int* __restrict__ bucket, int count,
                                              const TX* __restrict__ x, T* __restrict__ y, int blk, int nblk) {
     using Ly = Layout<N>;
@@ -624,7 +625,7 @@ __device__ __forceinline__ void element_body(const LevelView<T>& L, const int* _
             const bool interior = (r.info >> 12) & 1;
             const T* mg = L.mg + 7 * s.goff;
             const T* co = mg + (s.side == 0 ? 1 : 4) * s.q * s.q;
-            DG_Q_SWITCH(s.q, (lift_slot<N, Q, T, OR>(L, s, interior, r.sig, Y, sDL, sFT, F, mg, co, L.mt + 4 * s.goff,
+            DG_Q_SWITCH(s.q, (lift_slot<N, Q, T, OR, BDM>(L, s, interior, r.sig, Y, sDL, sFT, F, mg, co, L.mt + 4 * s.goff,
                                                  lane)))
         }
         for (int k = lane; k < N3; k += 32) y[dofo + k] = Y[k];
@@ -632,10 +633,12 @@ __device__ __forceinline__ void element_body(const LevelView<T>& L, const int* _
     }
 }
 
-template <int N, typename T, typename TX, bool OR>
+// BD: the block-diagonal apply of the Schwarz smoother (compiled apart so that
+// the ordinary apply carries no test for it).
+template <int N, typename T, typename TX, bool OR, bool BD = false>
 __global__ void element_kernel(LevelView<T> L, const int* __restrict__ bucket, int count, const TX* __restrict__ x,
                                T* __restrict__ y) {
-    element_body<N, T, TX, OR>(L, bucket, count, x, y, blockIdx.x, gridDim.x);
+    element_body<N, T, TX, OR, BD ? 1 : 0>(L, bucket, count, x, y, blockIdx.x, gridDim.x);
 }
 
 // All degree buckets of a level in one launch (used on small levels, where
@@ -883,13 +886,13 @@ cudaError_t launch_trace(const LevelView<T>& L, const BucketInfo& b, const TX* x
     return cudaGetLastError();
 }
 
-template <int N, typename T, typename TX, bool OR>
+template <int N, typename T, typename TX, bool OR, bool BD = false>
 cudaError_t launch_element(const LevelView<T>& L, const BucketInfo& b, const TX* x, T* y, cudaStream_t st) {
     using Ly = Layout<N>;
     static const LaunchShape shp = [&] {   // the mortar tables have the same size in every context
         LaunchShape r{};
         const size_t table_bytes = table_vals<N>(sizeof(T) == 4 ? L.ft.total : 0) * sizeof(T);
-        r.err = pick_warps(element_kernel<N, T, TX, OR>, table_bytes, Ly::EWARP * sizeof(T), r.W, r.smem, r.per_sm);
+        r.err = pick_warps(element_kernel<N, T, TX, OR, BD>, table_bytes, Ly::EWARP * sizeof(T), r.W, r.smem, r.per_sm);
         return r;
     }();
     if (shp.err != cudaSuccess) return shp.err;
@@ -897,7 +900,7 @@ cudaError_t launch_element(const LevelView<T>& L, const BucketInfo& b, const TX*
     const size_t smem = shp.smem;
     int grid = (b.count + W - 1) / W;
     if (grid > grid_cap() * per_sm) grid = grid_cap() * per_sm;
-    element_kernel<N, T, TX, OR><<<grid, W * 32, smem, st>>>(L, b.elems, b.count, x, y);
+    element_kernel<N, T, TX, OR, BD><<<grid, W * 32, smem, st>>>(L, b.elems, b.count, x, y);
     return cudaGetLastError();
 }
 
@@ -1041,6 +1044,8 @@ cudaError_t launch_path(int path, const LevelView<T>& L, const BucketInfo* bucke
                 DG_N_SWITCH(n, (err = apply_detail::launch_trace<NN, T, TX, true>(L, b, x, sj)))
             } else if (phase == 0) {
                 DG_N_SWITCH(n, (err = apply_detail::launch_trace<NN, T, TX, false>(L, b, x, sj)))
+            } else if (L.bdiag) {   // block-diagonal apply: the general (turned-interface) form
+                DG_N_SWITCH(n, (err = apply_detail::launch_element<NN, T, TX, true, true>(L, b, x, y, sj)))
             } else if (L.oriented) {
                 DG_N_SWITCH(n, (err = apply_detail::launch_element<NN, T, TX, true>(L, b, x, y, sj)))
             } else {
