@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define DGELL_VERSION 112
+#define DGELL_VERSION 113
 
 enum {
     DG_OK = 0,
@@ -314,6 +314,76 @@ int dg_newton_solve(dg_ctx* ctx, double* u, double tol_newton, int max_newton,
  * (eq. psi-interpolation); direction 1 = restriction of a weak residual,
  * out_H = (I_h^H)^T in_h (eq. temp-G).  Device vectors in prec. */
 int dg_transfer(dg_ctx* ctx, int coarse_level, int prec, int direction, const void* in, void* out);
+
+/* A-posteriori error estimator eta^2(e) of eq. (Eta2_Local) (Sec. II.D) on
+ * the finest level, for -Lap u + f u = g with Dirichlet data g_D:
+ *   eta^2(e) = h_e^2 p_e^2 ||f u - g - Lap u||^2_e
+ *            + sum over e's interior mortars of
+ *                h_m / p_m ||[[grad u]] . n||^2_m + sigma p_m^2 / h_m ||[[u]]||^2_m
+ *            + sum over e's Dirichlet mortars of sigma p_m^2 / h_m ||u - g_D||^2_m
+ * (eqs. Eta2_Ingredients, Eta2_Integrals, weights as printed there), with
+ * h_e the largest distance between two vertices of e, p_m, h_m and sigma
+ * those of the operator's penalty (eq. penaltyparameter), Lap u the exact
+ * Laplacian of the mapped polynomial on the isoparametric element, and
+ * every norm by the operator's own GL quadrature.  Each interior mortar's
+ * terms count in full for both of its elements.
+ * u: device double, n_dofs; g_qp, f_qp: device double values at the finest
+ * level's volume GL points (dg_quadrature_points order), NULL for 0 (pass
+ * the coefficient given to dg_set_zeroth_order as f_qp); gD_qp: device
+ * double values at the Dirichlet mortar points, NULL for 0.  eta2: device
+ * double, n_elems (output).  Single-box meshes only (DG_ERR_UNSUPPORTED with
+ * blocks).  Queues one FP64 apply of u (overwriting the level's trace
+ * buffer), a node-coordinate kernel and the estimator kernel; takes
+ * 4 n_dofs doubles of stream-ordered scratch (cudaMallocAsync) for the
+ * duration of the call.  Asynchronous. */
+int dg_estimate(dg_ctx* ctx, const double* u, const double* g_qp, const double* f_qp, const double* gD_qp,
+                double* eta2);
+
+/* hp-AMR driving strategy (Sec. II.D, Algorithm 4, smooth-pred).  Host code,
+ * no context and no GPU needed. */
+typedef enum { DG_AMR_NONE = 0, DG_AMR_P_REFINE = 1, DG_AMR_H_REFINE = 2 } dg_amr_action;
+typedef enum {
+    DG_MARK_FRACTION = 0,   /* refine the ceil(theta n) elements with the largest eta^2 (ties: lower index) */
+    DG_MARK_MEAN = 1        /* refine where eta^2 > theta * mean(eta^2) (sum in element order) */
+} dg_mark_kind;
+
+typedef struct {
+    int criterion;          /* dg_mark_kind */
+    double theta;           /* FRACTION: share of elements in (0, 1]; MEAN: factor on the mean */
+    double gamma_h;         /* Algorithm 4's gamma_h; <= 0 selects 0.25 */
+    double gamma_p;         /* Algorithm 4's gamma_p; <= 0 selects 0.1 */
+    int p_max;              /* largest degree; <= 0 selects 8 (the library's limit) */
+    int level_max;          /* deepest octree level; <= 0 selects 15 (the library's limit) */
+} dg_amr_opts;
+
+/* Marks elements (opts->criterion) and applies Algorithm 4 to each marked
+ * one: h-refine when eta2[e] > pred[e], else p-refine; a p-refinement at
+ * p_max becomes an h-refinement, an h-refinement at level_max a
+ * p-refinement (nothing when p = p_max too).  pred_next[e] is what the
+ * element carries on: gamma_p eta2[e] (p-refined), the prediction of each
+ * child gamma_h 2^-3 2^(-2 p_e) eta2[e] (h-refined), pred[e] (unchanged).
+ * Start with pred = +inf for the p-first start the text of Sec. II.D
+ * describes, 0 for Algorithm 4 taken literally.  All arrays HOST, n_elems
+ * long: eta2, pred, p, level (in), action (dg_amr_action), pred_next (out). */
+int dg_hp_mark(int n_elems, const double* eta2, const double* pred, const int* p, const int* level,
+               const dg_amr_opts* opts, int* action, double* pred_next);
+
+/* Applies the actions to a single-box leaf set (dg_mesh_desc leaves and p)
+ * and then refines further until every pair of face neighbours differs by
+ * at most one level (2:1).  h-refined elements become their 8 children
+ * (child c = i + 2 j + 4 k at (2 ix + i, 2 iy + j, 2 iz + k), in place of
+ * the parent) with the parent's degree and prediction pred_next[e];
+ * p-refined ones get p + 1; children of balance-only refinements keep the
+ * degree and get pred_init.  parent_out[k]: the input element new leaf k
+ * lies in.  HOST arrays.  *n_out receives the new element count; the
+ * outputs (leaves_out 4 per element, p_out, pred_out, parent_out; any may
+ * be NULL) are written when n_out <= max_out, else DG_ERR_INVALID is
+ * returned with *n_out set (call again with enough room).  DG_ERR_INVALID
+ * also for an h-refinement past level 15, a degree past 8, or leaves
+ * outside their level's index range. */
+int dg_hp_refine(int n_elems, const int* leaves, const int* p, const int* action, const double* pred_next,
+                 double pred_init, int max_out, int* n_out, int* leaves_out, int* p_out, double* pred_out,
+                 int* parent_out);
 
 /* Vector helpers used by the binding's tests and the bench (device memory,
  * on the context stream): precision conversion double <-> float. */

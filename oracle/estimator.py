@@ -129,45 +129,62 @@ def laplacian_at_gl(mesh, e, ue):
     return lap, u, w * detJ
 
 
-def estimate(mesh, u, g_fn=None, f_fn=None, gD_fn=None, C=10.0, parts=False):
-    """eta^2(e) for every element of `mesh` (oracle Mesh, single box).
+def _volume_term(mesh, e, u, g_fn, f_fn):
+    from .sipg import volume_points
+    ue = u[mesh.dof_off[e]:mesh.dof_off[e + 1]]
+    lap, uq, wd = laplacian_at_gl(mesh, e, ue)
+    xq = volume_points(mesh, e)
+    g = g_fn(xq) if g_fn is not None else 0.0
+    f = f_fn(xq) if f_fn is not None else 0.0
+    R = f * uq - g - lap
+    he = element_diameter(mesh, e)
+    pe = float(mesh.p[e])
+    return he * he * pe * pe * float(np.sum(wd * R * R))
+
+
+def _mortar_term(mesh, mi, u, gD_fn, C):
+    """eta^2_{m,1} + eta^2_{m,2} (interior) or eta^2_{m,3} (Dirichlet) of mortar mi."""
+    m = mesh.mortars[mi]
+    md = MortarData(mesh, mi, C)
+    hm = min(h.min() for h in md.h)
+    pm = float(m.pm)
+    uA = u[mesh.dof_off[m.eA]:mesh.dof_off[m.eA + 1]]
+    vA = md.psi[0] @ uA
+    if m.eB is None:
+        gD = gD_fn(md.x) if gD_fn is not None else 0.0
+        J3 = vA - gD
+        return md.sigma / hm * pm * pm * float(np.sum(md.W * J3 * J3))
+    uB = u[mesh.dof_off[m.eB]:mesh.dof_off[m.eB + 1]]
+    J1 = md.dn[0] @ uA - md.dn[1] @ uB
+    J2 = vA - md.psi[1] @ uB
+    return hm / pm * float(np.sum(md.W * J1 * J1)) + md.sigma / hm * pm * pm * float(np.sum(md.W * J2 * J2))
+
+
+def estimate(mesh, u, g_fn=None, f_fn=None, gD_fn=None, C=10.0, parts=False, elems=None):
+    """eta^2(e) for every element of `mesh` (oracle Mesh, single box), or for
+    the elements listed in `elems` only (in that order).
 
     u: nodal coefficients (n_dofs,); g_fn, f_fn, gD_fn: callables of physical
     points (P, 3) -> (P,) or None for zero.  With parts=True also returns the
-    per-element volume part and mortar part separately.
+    volume part and the mortar part separately.
     """
-    from .sipg import volume_points
     u = np.asarray(u, dtype=np.float64)
-    ne = mesh.n_elems
-    vol = np.zeros(ne)
-    mort = np.zeros(ne)
-    for e in range(ne):
-        ue = u[mesh.dof_off[e]:mesh.dof_off[e + 1]]
-        lap, uq, wd = laplacian_at_gl(mesh, e, ue)
-        xq = volume_points(mesh, e)
-        g = g_fn(xq) if g_fn is not None else 0.0
-        f = f_fn(xq) if f_fn is not None else 0.0
-        R = f * uq - g - lap
-        he = element_diameter(mesh, e)
-        pe = float(mesh.p[e])
-        vol[e] = he * he * pe * pe * float(np.sum(wd * R * R))
-    for mi, m in enumerate(mesh.mortars):
-        md = MortarData(mesh, mi, C)
-        hm = min(h.min() for h in md.h)
-        pm = float(m.pm)
-        uA = u[mesh.dof_off[m.eA]:mesh.dof_off[m.eA + 1]]
-        vA = md.psi[0] @ uA
-        if m.eB is None:
-            gD = gD_fn(md.x) if gD_fn is not None else 0.0
-            J3 = vA - gD
-            mort[m.eA] += md.sigma / hm * pm * pm * float(np.sum(md.W * J3 * J3))
-            continue
-        uB = u[mesh.dof_off[m.eB]:mesh.dof_off[m.eB + 1]]
-        J1 = md.dn[0] @ uA - md.dn[1] @ uB
-        J2 = vA - md.psi[1] @ uB
-        t = hm / pm * float(np.sum(md.W * J1 * J1)) + md.sigma / hm * pm * pm * float(np.sum(md.W * J2 * J2))
-        mort[m.eA] += t
-        mort[m.eB] += t
+    sel = list(range(mesh.n_elems)) if elems is None else [int(e) for e in elems]
+    pos = {e: i for i, e in enumerate(sel)}
+    vol = np.zeros(len(sel))
+    mort = np.zeros(len(sel))
+    for i, e in enumerate(sel):
+        vol[i] = _volume_term(mesh, e, u, g_fn, f_fn)
+    if elems is None:
+        mortars = range(len(mesh.mortars))
+    else:
+        mortars = sorted({mi for e in sel for f in range(6) for mi in mesh.elem_mortars[e][f]})
+    for mi in mortars:
+        m = mesh.mortars[mi]
+        t = _mortar_term(mesh, mi, u, gD_fn, C)
+        for e in (m.eA, m.eB):
+            if e is not None and e in pos:
+                mort[pos[e]] += t
     if parts:
         return vol + mort, vol, mort
     return vol + mort

@@ -10,6 +10,7 @@
 #include "context.h"
 #include "geom.h"
 #include "source.h"
+#include "estimate.h"
 
 using namespace dg;
 
@@ -509,6 +510,27 @@ int vcycle_maybe_graph(dg_ctx* c, int prec, double* r, double* v, const dg_mg_op
     return DG_OK;
 }
 
+GeomArgs geom_args(dg_ctx* c, const LevelDev& L) {
+    GeomArgs g{};
+    g.n_elems = L.h.n_elems();
+    g.leaves = L.leaves;
+    g.p = L.p;
+    g.dof_off = L.dof_off;
+    g.vqp_off = L.vqp_off;
+    g.tab = c->tab64;
+    for (int d = 0; d < 3; ++d) {
+        g.lo[d] = c->desc.lo[d];
+        g.hi[d] = c->desc.hi[d];
+        g.warp_k[d] = c->desc.warp_k[d];
+    }
+    g.map_kind = c->desc.map_kind;
+    g.warp_amp = c->desc.warp_amp;
+    g.n_blocks = (int)c->blocks.size();
+    g.blocks = c->blocks_dev;
+    g.block = L.block;
+    return g;
+}
+
 int upload_level(dg_ctx* c, LevelDev& L, int li, std::string& err) {
     Arena& A = c->arena;
     cudaStream_t st = c->st;
@@ -567,23 +589,7 @@ int upload_level(dg_ctx* c, LevelDev& L, int li, std::string& err) {
         return DG_ERR_OOM;
     }
     cudaMemsetAsync(bad, 0, sizeof(int), st);
-    GeomArgs g{};
-    g.n_elems = h.n_elems();
-    g.leaves = L.leaves;
-    g.p = L.p;
-    g.dof_off = L.dof_off;
-    g.vqp_off = L.vqp_off;
-    g.tab = c->tab64;
-    for (int d = 0; d < 3; ++d) {
-        g.lo[d] = c->desc.lo[d];
-        g.hi[d] = c->desc.hi[d];
-        g.warp_k[d] = c->desc.warp_k[d];
-    }
-    g.map_kind = c->desc.map_kind;
-    g.warp_amp = c->desc.warp_amp;
-    g.n_blocks = (int)c->blocks.size();
-    g.blocks = c->blocks_dev;
-    g.block = L.block;
+    const GeomArgs g = geom_args(c, L);
     cudaError_t e1 = launch_node_coords(g, X, st);
     cudaError_t e2 = launch_volume_geom(g, X, L.G64, L.wdetJ, L.vxyz, nv, bad, st);
     cudaError_t e3 = launch_mortar_geom(g, X, L.mortars, nmort, c->C, L.mg64, L.sigma64, L.bxyz, nb, bad, st);
@@ -842,6 +848,44 @@ int dg_apply(dg_ctx* c, int level, int prec, const void* x, void* y) {
         return DG_OK;
     }
     return fail(DG_ERR_UNSUPPORTED, "precision not implemented");
+}
+
+int dg_estimate(dg_ctx* c, const double* u, const double* g_qp, const double* f_qp, const double* gD_qp,
+                double* eta2) {
+    if (!c || !u || !eta2) return fail(DG_ERR_INVALID, "NULL argument");
+    if (!c->blocks.empty()) return fail(DG_ERR_UNSUPPORTED, "dg_estimate: single-box meshes only");
+    const int l = (int)c->lv.size() - 1;
+    LevelDev& L = c->lv[l];
+    const long long nd = L.h.n_dofs();
+    if (L.h.n_elems() == 0) return DG_OK;
+    double* X = nullptr;   // node coordinates (3 nd) and the apply's output (nd), stream-ordered
+    CK(cudaMallocAsync((void**)&X, sizeof(double) * 4 * nd, c->st));
+    double* y = X + 3 * nd;
+    cudaError_t e = launch_node_coords(geom_args(c, L), X, c->st);
+    int rc = e == cudaSuccess ? apply_t<double>(c, l, u, y) : DG_OK;   // fills the trace buffer with u's traces
+    if (e == cudaSuccess && rc == DG_OK) {
+        EstimateArgs a{};
+        a.n_elems = L.h.n_elems();
+        a.p = L.p;
+        a.dof_off = L.dof_off;
+        a.vqp_off = L.vqp_off;
+        a.slot_off = L.slot_off;
+        a.slot_mortar = L.slot_mortar;
+        a.mortars = L.mortars;
+        a.mg = L.mg64;
+        a.sigma = L.sigma64;
+        a.mt = L.mt64;
+        a.tab = c->tab64;
+        a.X = X;
+        a.C = c->C;
+        e = launch_estimate(a, u, g_qp, f_qp, gD_qp, eta2, c->st);
+        c->launches += 2;
+    }
+    cudaError_t ef = cudaFreeAsync(X, c->st);
+    if (e != cudaSuccess) return fail(DG_ERR_CUDA, cudaGetErrorString(e));
+    if (rc != DG_OK) return rc;
+    if (ef != cudaSuccess) return fail(DG_ERR_CUDA, cudaGetErrorString(ef));
+    return DG_OK;
 }
 
 int dg_convert(dg_ctx* c, int64_t n, int sp, const void* s, int dp, void* d) {

@@ -74,6 +74,14 @@ class dg_puncture_params(ctypes.Structure):
                 ("P", (ctypes.c_double * 3) * 16)]
 
 
+class dg_amr_opts(ctypes.Structure):
+    _fields_ = [("criterion", ctypes.c_int), ("theta", ctypes.c_double), ("gamma_h", ctypes.c_double),
+                ("gamma_p", ctypes.c_double), ("p_max", ctypes.c_int), ("level_max", ctypes.c_int)]
+
+
+DG_AMR_NONE, DG_AMR_P_REFINE, DG_AMR_H_REFINE = 0, 1, 2
+DG_MARK_FRACTION, DG_MARK_MEAN = 0, 1
+
 _P = ctypes.c_void_p
 _SIGS = {
     "dg_version": ([], ctypes.c_int),
@@ -101,6 +109,10 @@ _SIGS = {
     "dg_launch_count": ([_P], ctypes.c_int64),
     "dg_transfer": ([_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P], ctypes.c_int),
     "dg_smooth_static": ([_P, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.POINTER(dg_cheb_opts), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "dg_estimate": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "dg_hp_mark": ([ctypes.c_int, _P, _P, _P, _P, ctypes.POINTER(dg_amr_opts), _P, _P], ctypes.c_int),
+    "dg_hp_refine": ([ctypes.c_int, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                      _P, _P, _P, _P], ctypes.c_int),
 }
 
 _lib = None
@@ -193,6 +205,49 @@ def make_mesh_desc(desc):
     return d
 
 
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def hp_mark(eta2, pred, p, level, criterion=DG_MARK_FRACTION, theta=0.1, gamma_h=0.25, gamma_p=0.1, p_max=8,
+            level_max=15):
+    """dg_hp_mark on host arrays: returns (action, pred_next) as numpy arrays."""
+    n = len(eta2)
+    e, ep = _host(eta2, np.float64)
+    q, qp = _host(pred, np.float64)
+    pp, ppp = _host(p, np.int32)
+    lv, lvp = _host(level, np.int32)
+    act = np.zeros(n, dtype=np.int32)
+    nxt = np.zeros(n, dtype=np.float64)
+    o = dg_amr_opts(criterion, theta, gamma_h, gamma_p, p_max, level_max)
+    _check(lib().dg_hp_mark(n, ep, qp, ppp, lvp, ctypes.byref(o), act.ctypes.data_as(ctypes.c_void_p),
+                            nxt.ctypes.data_as(ctypes.c_void_p)))
+    return act, nxt
+
+
+def hp_refine(leaves, p, action, pred_next, pred_init=float("inf")):
+    """dg_hp_refine on host arrays: returns (leaves (n, 4), p, pred, parent)."""
+    n = len(p)
+    lv, lvp = _host(np.asarray(leaves).reshape(-1, 4), np.int32)
+    pp, ppp = _host(p, np.int32)
+    a, ap = _host(action, np.int32)
+    q, qp = _host(pred_next, np.float64)
+    cnt = ctypes.c_int(0)
+    rc = lib().dg_hp_refine(n, lvp, ppp, ap, qp, pred_init, 0, ctypes.byref(cnt), None, None, None, None)
+    if rc not in (DG_OK, DG_ERR_INVALID) or (rc == DG_ERR_INVALID and cnt.value == 0 and n > 0):
+        _check(rc)
+    m = cnt.value
+    L = np.zeros((m, 4), dtype=np.int32)
+    P = np.zeros(m, dtype=np.int32)
+    Q = np.zeros(m, dtype=np.float64)
+    R = np.zeros(m, dtype=np.int32)
+    _check(lib().dg_hp_refine(n, lvp, ppp, ap, qp, pred_init, m, ctypes.byref(cnt),
+                              L.ctypes.data_as(ctypes.c_void_p), P.ctypes.data_as(ctypes.c_void_p),
+                              Q.ctypes.data_as(ctypes.c_void_p), R.ctypes.data_as(ctypes.c_void_p)))
+    return L, P, Q, R
+
+
 def dg_version():
     return lib().dg_version()
 
@@ -278,6 +333,10 @@ class Context:
 
     def rhs(self, g_qp, gD_qp, F):
         _check(lib().dg_rhs(self.h, _ptr(g_qp), _ptr(gD_qp), _ptr(F)))
+
+    def estimate(self, u, eta2, g_qp=None, f_qp=None, gD_qp=None):
+        """eta^2(e) of the finest level into eta2 (device double, n_elems)."""
+        _check(lib().dg_estimate(self.h, _ptr(u), _ptr(g_qp), _ptr(f_qp), _ptr(gD_qp), _ptr(eta2)))
         return F
 
     def smooth(self, b, x, level=-1, n_eigs=15, n_cheb=15, Lambda=20.0, want_lambda=True):
