@@ -333,11 +333,12 @@ class Context:
 
     def rhs(self, g_qp, gD_qp, F):
         _check(lib().dg_rhs(self.h, _ptr(g_qp), _ptr(gD_qp), _ptr(F)))
+        return F
 
     def estimate(self, u, eta2, g_qp=None, f_qp=None, gD_qp=None):
         """eta^2(e) of the finest level into eta2 (device double, n_elems)."""
         _check(lib().dg_estimate(self.h, _ptr(u), _ptr(g_qp), _ptr(f_qp), _ptr(gD_qp), _ptr(eta2)))
-        return F
+        return eta2
 
     def smooth(self, b, x, level=-1, n_eigs=15, n_cheb=15, Lambda=20.0, want_lambda=True):
         o = cheb_opts(n_eigs, n_cheb, Lambda)
