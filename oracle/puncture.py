@@ -9,13 +9,20 @@ and its linearisation J_R du = -Lap du + 7 alpha beta (1 + alpha (1 + u))^-8 du
 evaluated at the volume GL points after interpolating u there (Sec. III.B).
 
 Readings:
- * Zero spin: A_ij = sum_I 3 / (2 r_I^2) [P_i n_j + P_j n_i - (delta_ij - n_i n_j) P.n]
-   (the printed spin term is garbled; the workloads use S = 0).
+ * A_ij = sum_I { 3 / (2 r_I^2) [P_i n_j + P_j n_i - (delta_ij - n_i n_j) P.n]
+                 + 3 / r_I^3 [n_i (S x n)_j + n_j (S x n)_i] }.
+   The printed spin term, (4 / r) n_(i eps_j)kl S^k n^l inside the bracket
+   that 3 / (2 r^2) multiplies, is read with the symmetrisation
+   t_(ij) = (t_ij + t_ji) / 2 and eps_jkl S^k n^l = (S x n)_j, which gives
+   the 3 / r^3 term above; punctures without a spin vector have S = 0.
  * Outer boundary: u = 0 Dirichlet on the box (u -> 0 at infinity).
  * Newton loop: while k < N_NK and ||R(u_k)|| >= tol_NK (Alg. 1 joins the two
    tests with "or").
 
-Pins: single-puncture closed form A_ij A^ij = 9 / (2 r^4) (|P|^2 + 2 (P.n)^2),
+Pins: single-puncture closed forms A_ij A^ij = 9 / (2 r^4) (|P|^2 + 2 (P.n)^2)
+and, for a spin alone, 18 (|S|^2 - (S.n)^2) / r^6; A_ij symmetric, traceless
+and divergence-free (the flat momentum constraint, by finite differences)
+with momenta and spins together,
 J_R v against a central finite difference of R, quadratic Newton
 convergence (tests/test_oracle_puncture.py).
 
@@ -29,13 +36,16 @@ import numpy as np
 from . import tables, sipg
 
 
-def alpha_beta(x, punctures):
-    """alpha and beta at points x (P, 3); punctures: list of (m, c(3), P(3))."""
+def extrinsic_curvature(x, punctures):
+    """A_ij (P, 3, 3) and 1/alpha at points x (P, 3); punctures: list of
+    (m, c(3), P(3)) or (m, c(3), P(3), S(3))."""
     x = np.asarray(x, dtype=np.float64)
     inv_alpha = np.zeros(len(x))
     A = np.zeros((len(x), 3, 3))
     I3 = np.eye(3)
-    for (m, c, P) in punctures:
+    for pu in punctures:
+        m, c, P = pu[0], pu[1], pu[2]
+        S = np.asarray(pu[3] if len(pu) > 3 else (0.0, 0.0, 0.0), dtype=np.float64)
         dx = x - np.asarray(c, dtype=np.float64)
         r = np.linalg.norm(dx, axis=1)
         nvec = dx / r[:, None]
@@ -44,7 +54,17 @@ def alpha_beta(x, punctures):
         term = (np.einsum('i,pj->pij', P, nvec) + np.einsum('pi,j->pij', nvec, P)
                 - (I3[None] - np.einsum('pi,pj->pij', nvec, nvec)) * Pn[:, None, None])
         A += (1.5 / r ** 2)[:, None, None] * term
+        Sxn = np.cross(S[None, :], nvec)
+        spin = np.einsum('pi,pj->pij', nvec, Sxn) + np.einsum('pi,pj->pij', Sxn, nvec)
+        A += (3.0 / r ** 3)[:, None, None] * spin
         inv_alpha += m / (2.0 * r)
+    return A, inv_alpha
+
+
+def alpha_beta(x, punctures):
+    """alpha and beta at points x (P, 3); punctures: list of (m, c(3), P(3))
+    or (m, c(3), P(3), S(3))."""
+    A, inv_alpha = extrinsic_curvature(x, punctures)
     AA = np.einsum('pij,pij->p', A, A)
     alpha = 1.0 / inv_alpha
     beta = alpha ** 7 * AA / 8.0

@@ -220,6 +220,16 @@ def three_punctures(seed=2):
     return out
 
 
+def table_punctures():
+    """The three spinning punctures of Sec. III.D (table Multi_Punctures):
+    mass m, position (x, y, 0), momentum (P_x, P_y, 0) and spin (0, 0, S_z)
+    as printed there."""
+    rows = [(0.2691, 0.0152, -0.6933, 0.0585, 0.0082, -0.0134),
+            (0.4063, -2.316, 1.8274, -0.0284, -0.1497, -0.0332),
+            (0.3245, -1.0279, -2.2711, 0.1640, 0.0515, -0.0708)]
+    return [(m, (x, y, 0.0), (px, py, 0.0), (0.0, 0.0, sz)) for (m, x, y, px, py, sz) in rows]
+
+
 def puncture_mesh(punctures, R=24.0, level=3, refine=2, p_base=4, p_fine=6):
     """Box [-R, R]^3, cells within one cell width of a puncture refined `refine`
     times (2:1 balanced); p_fine on the finest cells, p_base elsewhere."""
