@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define DGELL_VERSION 113
+#define DGELL_VERSION 114
 
 enum {
     DG_OK = 0,
@@ -265,14 +265,18 @@ int dg_solve(dg_ctx* ctx, const double* b, double* x, const dg_solver_opts* opts
  * O^H = I^T O^h I of eq. (operator_oh) as dense per-element blocks. */
 int dg_set_zeroth_order(dg_ctx* ctx, const double* coef_qp);
 
-/* Puncture initial data (Sec. III.D, zero spin):
+/* Puncture initial data (Sec. III.D, eqs. Two_Punctures_PDE, Two_Punctures_Aij):
  * R(u) = -Lap u - beta (1 + alpha (1 + u))^-7, u = 0 on the box boundary,
- * 1/alpha = sum m_I / (2 r_I), beta = alpha^7 A_ij A^ij / 8. */
+ * 1/alpha = sum m_I / (2 r_I), beta = alpha^7 A_ij A^ij / 8,
+ * A_ij = sum_I 3 / (2 r_I^2) [P_i n_j + P_j n_i - (delta_ij - n_i n_j) P.n]
+ *      + 3 / r_I^3 [n_i (S x n)_j + n_j (S x n)_i]
+ * (the printed spin term read with t_(ij) = (t_ij + t_ji) / 2). */
 typedef struct {
     int n;                 /* number of punctures, <= 16 */
     double m[16];
     double c[16][3];       /* positions */
     double P[16][3];       /* linear momenta */
+    double S[16][3];       /* spins (zero for non-spinning punctures) */
 } dg_puncture_params;
 
 /* Evaluates alpha, beta at the finest level's volume GL points and keeps

@@ -247,6 +247,7 @@ int dg_puncture_setup(dg_ctx* c, const dg_puncture_params* prm) {
         for (int k = 0; k < 3; ++k) {
             P.c[i][k] = prm->c[i][k];
             P.P[i][k] = prm->P[i][k];
+            P.S[i][k] = prm->S[i][k];
         }
     }
     LevelDev& F = c->lv.back();

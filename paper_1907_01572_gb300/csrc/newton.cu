@@ -10,8 +10,9 @@
 //   this per descendant in sum-factorised form (first over the z points for
 //   every pair (c, c'), then over x and y per matrix entry).
 // * Puncture: 1/alpha = sum_I m_I / (2 r_I); A_ij = sum_I 3/(2 r_I^2)
-//   [P_i n_j + P_j n_i - (delta_ij - n_i n_j) P.n] (zero spin);
-//   beta = alpha^7 A_ij A_ij / 8.  Source s(u) = beta (1 + alpha (1 + u))^-7,
+//   [P_i n_j + P_j n_i - (delta_ij - n_i n_j) P.n] + 3/r_I^3 [n_i w_j + n_j w_i],
+//   w = S_I x n (the spin term of eq. Two_Punctures_Aij, its symmetrisation
+//   taken as t_(ij) = (t_ij + t_ji) / 2); beta = alpha^7 A_ij A_ij / 8.  Source s(u) = beta (1 + alpha (1 + u))^-7,
 //   Jacobian coefficient f(u) = 7 alpha beta (1 + alpha (1 + u))^-8.
 // * Power-law source (the constant-density star of Sec. III.C,
 //   Lap psi + 2 pi rho psi^5 = 0): s(u) = c u^k, f(u) = -k c u^(k-1), with c
@@ -43,10 +44,13 @@ __global__ void puncture_kernel(const double* vxyz, long long n, PunctureDev P, 
             double nv[3];
             for (int k = 0; k < 3; ++k) nv[k] = dx[k] / r;
             const double Pn = P.P[I][0] * nv[0] + P.P[I][1] * nv[1] + P.P[I][2] * nv[2];
-            const double f = 1.5 / r2;
+            const double f = 1.5 / r2, fs = 3.0 / (r2 * r);
+            const double w[3] = {P.S[I][1] * nv[2] - P.S[I][2] * nv[1], P.S[I][2] * nv[0] - P.S[I][0] * nv[2],
+                                 P.S[I][0] * nv[1] - P.S[I][1] * nv[0]};   // S x n
             for (int a = 0; a < 3; ++a)
                 for (int b = 0; b < 3; ++b)
-                    A[a][b] += f * (P.P[I][a] * nv[b] + P.P[I][b] * nv[a] - ((a == b ? 1.0 : 0.0) - nv[a] * nv[b]) * Pn);
+                    A[a][b] += f * (P.P[I][a] * nv[b] + P.P[I][b] * nv[a] - ((a == b ? 1.0 : 0.0) - nv[a] * nv[b]) * Pn) +
+                               fs * (nv[a] * w[b] + nv[b] * w[a]);
             inv_a += P.m[I] / (2.0 * r);
         }
         double AA = 0.0;

@@ -9,6 +9,7 @@ struct PunctureDev {
     double m[16];
     double c[16][3];
     double P[16][3];
+    double S[16][3];
 };
 
 enum NlKind { kNlNone = 0, kNlPuncture = 1, kNlPower = 2 };

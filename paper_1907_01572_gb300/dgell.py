@@ -71,7 +71,7 @@ class dg_solve_stats(ctypes.Structure):
 
 class dg_puncture_params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("m", ctypes.c_double * 16), ("c", (ctypes.c_double * 3) * 16),
-                ("P", (ctypes.c_double * 3) * 16)]
+                ("P", (ctypes.c_double * 3) * 16), ("S", (ctypes.c_double * 3) * 16)]
 
 
 class dg_amr_opts(ctypes.Structure):
@@ -374,11 +374,14 @@ class Context:
     def puncture_setup(self, punctures):
         prm = dg_puncture_params()
         prm.n = len(punctures)
-        for i, (m, c, P) in enumerate(punctures):
+        for i, pu in enumerate(punctures):
+            m, c, P = pu[0], pu[1], pu[2]
+            S = pu[3] if len(pu) > 3 else (0.0, 0.0, 0.0)
             prm.m[i] = m
             for k in range(3):
                 prm.c[i][k] = c[k]
                 prm.P[i][k] = P[k]
+                prm.S[i][k] = S[k]
         _check(lib().dg_puncture_setup(self.h, ctypes.byref(prm)))
 
     def puncture_residual(self, u, R):

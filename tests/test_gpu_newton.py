@@ -96,6 +96,37 @@ def test_newton_solve_matches_oracle():
     ctx.close()
 
 
+def test_spinning_punctures_residual_and_newton_match_oracle():
+    """The three spinning punctures of the paper's table (momenta and spins):
+    residual within 1e-12 of the oracle's, Newton (FP64 and FP32 V-cycle)
+    within 1e-8 of the oracle's exact-solve Newton."""
+    import torch
+    from paper_1907_01572_gb300 import dgell
+    punc = inputs.table_punctures()
+    desc = _puncture_mesh(level=2, p=3)
+    m = Mesh(desc["lo"], desc["hi"], desc["leaves"], desc["p"])
+    prob = puncture.PunctureProblem(m, punc)
+    ctx = dgell.Context(desc)
+    ctx.puncture_setup(punc)
+    u = 0.05 * inputs.random_vector(m.n_dofs, seed=6)
+    R = torch.empty(m.n_dofs, dtype=torch.float64, device="cuda")
+    ctx.puncture_residual(torch.tensor(u, device="cuda"), R)
+    assert rel_l2(R.cpu().numpy(), prob.residual(u)) < 1e-12
+    nospin = puncture.PunctureProblem(m, [pu[:3] for pu in punc])
+    assert rel_l2(nospin.residual(u), prob.residual(u)) > 1e-6     # the spins matter here
+
+    def ls(coef, rhs):
+        return spla.spsolve(sipg.assemble(m, 10.0, coef=coef).tocsc(), rhs)
+
+    uo, ko, hist = puncture.newton(prob, np.zeros(m.n_dofs), ls, tol=1e-12)
+    for prec in (dgell.DG_FP64, dgell.DG_FP32):
+        x = torch.zeros(m.n_dofs, dtype=torch.float64, device="cuda")
+        steps, rn = ctx.newton_solve(x, tol_newton=1e-10 * hist[0], max_newton=10, mg_prec=prec, tol=1e-11)
+        assert rn < 1e-10 * hist[0] and steps <= ko + 2, (steps, rn, hist)
+        assert rel_l2(x.cpu().numpy(), uo) < 1e-8
+    ctx.close()
+
+
 def test_newton_step_first_call_and_guards():
     """A Newton step as the first call on a fresh context, and the error for a
     Newton call before dg_puncture_setup."""
