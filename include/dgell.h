@@ -353,7 +353,8 @@ typedef enum {
 
 typedef struct {
     int criterion;          /* dg_mark_kind */
-    double theta;           /* FRACTION: share of elements in (0, 1]; MEAN: factor on the mean */
+    double theta;           /* FRACTION: share of elements in (0, 1]; MEAN: factor >= 0 on the mean
+                               (DG_ERR_INVALID outside these ranges) */
     double gamma_h;         /* Algorithm 4's gamma_h; <= 0 selects 0.25 */
     double gamma_p;         /* Algorithm 4's gamma_p; <= 0 selects 0.1 */
     int p_max;              /* largest degree; <= 0 selects 8 (the library's limit) */

@@ -38,6 +38,10 @@ NONE, P_REFINE, H_REFINE = 0, 1, 2
 def mark(eta2, criterion, theta):
     """Booleans: which elements Algorithm 4 treats as having a large eta^2."""
     n = len(eta2)
+    if criterion == 'fraction' and not 0.0 < theta <= 1.0:
+        raise ValueError("the fraction criterion takes theta in (0, 1]")
+    if criterion == 'mean' and not (theta >= 0.0 and math.isfinite(theta)):
+        raise ValueError("the mean criterion takes a finite theta >= 0")
     if n == 0:
         return []
     if criterion == 'fraction':

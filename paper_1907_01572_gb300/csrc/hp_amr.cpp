@@ -52,14 +52,17 @@ extern "C" int dg_hp_mark(int n, const double* eta2, const double* pred, const i
         return dgi_set_error(DG_ERR_INVALID, "dg_hp_mark: NULL argument");
     if (o->criterion != DG_MARK_FRACTION && o->criterion != DG_MARK_MEAN)
         return dgi_set_error(DG_ERR_INVALID, "dg_hp_mark: unknown criterion");
+    if (o->criterion == DG_MARK_FRACTION ? !(o->theta > 0.0 && o->theta <= 1.0)
+                                         : !(o->theta >= 0.0 && std::isfinite(o->theta)))
+        return dgi_set_error(DG_ERR_INVALID, "dg_hp_mark: theta outside (0, 1] (fraction) or [0, inf) (mean)");
     const double gh = o->gamma_h > 0 ? o->gamma_h : 0.25;
     const double gp = o->gamma_p > 0 ? o->gamma_p : 0.1;
     const int pmax = o->p_max > 0 ? o->p_max : kMaxP;
     const int lmax = o->level_max > 0 ? o->level_max : kMaxLevel;
     std::vector<char> marked(n, 0);
     if (o->criterion == DG_MARK_FRACTION) {
-        const int k = (int)std::ceil(o->theta * n);
-        const int kk = k < 0 ? 0 : (k > n ? n : k);
+        const double kd = std::ceil(o->theta * n);   // theta in (0, 1]: 1 <= kd <= n
+        const int kk = kd > n ? n : (int)kd;
         std::vector<int> order(n);
         std::iota(order.begin(), order.end(), 0);
         // the kk largest, ties to the lower index: a strict weak order on (-eta2, e)

@@ -78,3 +78,16 @@ def test_refine_order_children_in_place_and_errors():
         dgell.hp_refine([(0, 0, 0, 0)], [8], [dgell.DG_AMR_P_REFINE], [0.0])
     with pytest.raises(dgell.DgError):
         dgell.hp_refine([(1, 2, 0, 0)], [3], [0], [0.0])
+
+
+def test_mark_rejects_bad_theta():
+    eta = np.ones(4)
+    z = np.zeros(4)
+    p = np.full(4, 2)
+    for crit, th in ((dgell.DG_MARK_FRACTION, 0.0), (dgell.DG_MARK_FRACTION, 1.5), (dgell.DG_MARK_FRACTION, math.nan),
+                     (dgell.DG_MARK_MEAN, -1.0), (dgell.DG_MARK_MEAN, math.inf), (dgell.DG_MARK_MEAN, math.nan)):
+        with pytest.raises(dgell.DgError):
+            dgell.hp_mark(eta, z, p, p, crit, th)
+    for crit, th in (('fraction', 0.0), ('fraction', 1.5), ('mean', -1.0), ('mean', math.inf)):
+        with pytest.raises(ValueError):
+            hpamr.mark(list(eta), crit, th)
