@@ -146,7 +146,7 @@ def test_element_schwarz_smoother():
     for n in (3, 5, 4):
         B = rng.standard_normal((n, n))
         blocks.append(B @ B.T + n * np.eye(n))
-    A = sp.block_diag(blocks, format="csr")
+    A = sp.block_diag([sp.csr_matrix(B) for B in blocks], format="csr")
     off = np.array([0, 3, 8, 12])
     b = rng.standard_normal(12)
     x = multigrid.schwarz_smoother(A, multigrid.schwarz_blocks(A, off), off, np.zeros(12), b, 1, 1.0)
