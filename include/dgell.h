@@ -47,7 +47,7 @@ enum {
     DG_ERR_CUDA = 3,           /* a CUDA runtime call failed */
     DG_ERR_NOT_CONVERGED = 4,  /* iteration cap reached; statistics are filled */
     DG_ERR_BREAKDOWN = 5,      /* non-finite or non-positive Krylov scalar */
-    DG_ERR_UNSUPPORTED = 6     /* valid request this build does not implement */
+    DG_ERR_UNSUPPORTED = 6     /* valid request this library version does not implement */
 };
 
 typedef enum { DG_FP64 = 0, DG_FP32 = 1, DG_BF16 = 2 } dg_prec;
