@@ -26,9 +26,10 @@ HBM_FALLBACK = 6800.0
 # kernels of that library version (profiles/apply_sweep32_traffic_v4.md,
 # profiles/apply_sweep32_traffic_v105.md, _v106.md, _v108.md, _v110.md, _v112.md); null for other
 # versions.  Version 109 changed only the nonlinear-source kernels; its apply kernels are those of 108.
-# Versions 113 (estimator, hp-AMR calls) and 114 (puncture spins) keep the apply kernels of 112.
+# Versions 113 (estimator, hp-AMR calls), 114 (puncture spins) and 115 (block-mesh refinement, host
+# code) keep the apply kernels of 112.
 TRAFFIC_BYTES_PER_APPLY = {104: 1.3634e9, 105: 1.3709e9, 106: 1.3770e9, 108: 1.3775e9, 109: 1.3775e9,
-                           110: 1.3774e9, 112: 1.3770e9, 113: 1.3770e9, 114: 1.3770e9}
+                           110: 1.3774e9, 112: 1.3770e9, 113: 1.3770e9, 114: 1.3770e9, 115: 1.3770e9}
 
 
 def peaks():

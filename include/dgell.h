@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define DGELL_VERSION 114
+#define DGELL_VERSION 115
 
 enum {
     DG_OK = 0,
@@ -389,6 +389,17 @@ int dg_hp_mark(int n_elems, const double* eta2, const double* pred, const int* p
 int dg_hp_refine(int n_elems, const int* leaves, const int* p, const int* action, const double* pred_next,
                  double pred_init, int max_out, int* n_out, int* leaves_out, int* p_out, double* pred_out,
                  int* parent_out);
+
+/* dg_hp_refine for any mesh description (dg_ctx_create's): with blocks,
+ * leaves are refined and 2:1-balanced inside their blocks and across block
+ * interfaces (the block connectivity found as for dg_ctx_create); children
+ * stay in their parent's block (block_out, may be NULL).  mesh->leaves,
+ * mesh->p and mesh->elem_block are the input elements; action and pred_next
+ * are n_elems long.  Same outputs, ordering and errors as dg_hp_refine, plus
+ * DG_ERR_INVALID for a bad block description. */
+int dg_hp_refine_mesh(const dg_mesh_desc* mesh, const int* action, const double* pred_next, double pred_init,
+                      int max_out, int* n_out, int* leaves_out, int* p_out, int* block_out, double* pred_out,
+                      int* parent_out);
 
 /* Vector helpers used by the binding's tests and the bench (device memory,
  * on the context stream): precision conversion double <-> float. */

@@ -26,11 +26,19 @@ Readings (where the paper leaves the choice open or disagrees with itself):
    balance-only refinements keep the degree and start with the initial
    prediction.
 
-Pins: hand-worked marking, decisions and a balance cascade; the 2:1 and
-tiling invariants through the oracle mesh constructor
-(tests/test_oracle_hpamr.py).
+Multi-block meshes (refine_blocks): the same actions, and 2:1 balance
+across block interfaces found physically: the point just outside the centre
+of each leaf face is mapped with the leaf's block map and located in every
+block by Newton's method on that block's map; the leaf of that block
+covering the point is the face neighbour to compare with.
+
+Pins: hand-worked marking, decisions and balance cascades (one box, and
+across a turned block interface); the 2:1 and tiling invariants through the
+oracle mesh constructors (tests/test_oracle_hpamr.py).
 """
 import math
+
+import numpy as np
 
 NONE, P_REFINE, H_REFINE = 0, 1, 2
 
@@ -134,3 +142,74 @@ def refine(leaves, p, action, pred_next, pred_init):
             pe, _, parent = out.pop(lf)
             for c in _children(lf):
                 out[c] = (pe, float(pred_init), parent)
+
+
+def _locate(blocks, x, tol=1e-9, iters=60):
+    """(block, reference point) of each physical point x (P, 3), or (-1, None)
+    outside every block: Newton's method on each block map from its centre."""
+    from .blockmesh import block_jacobian, block_map
+    P = len(x)
+    where = np.full(P, -1)
+    ref = np.zeros((P, 3))
+    for b, blk in enumerate(blocks):
+        todo = np.nonzero(where < 0)[0]
+        if len(todo) == 0:
+            break
+        xi = np.zeros((len(todo), 3))
+        for _ in range(iters):
+            r = block_map(blk, xi) - x[todo]
+            step = np.linalg.solve(block_jacobian(blk, xi), r[:, :, None])[:, :, 0]
+            xi = np.clip(xi - step, -3.0, 3.0)
+            if np.abs(step).max() < 1e-14:
+                break
+        ok = (np.abs(block_map(blk, xi) - x[todo]).max(axis=1) <= 1e-10 * np.maximum(1.0, np.abs(x[todo]).max(axis=1))) \
+            & (np.abs(xi).max(axis=1) <= 1.0 + tol)
+        where[todo[ok]] = b
+        ref[todo[ok]] = xi[ok]
+    return where, ref
+
+
+def refine_blocks(blocks, elem_block, leaves, p, action, pred_next, pred_init):
+    """refine() for a multi-block mesh: returns {(block, level, ix, iy, iz):
+    (p, pred, parent)}."""
+    from .blockmesh import block_map
+    out = {}
+    for e, lf in enumerate(leaves):
+        b = int(elem_block[e])
+        L, ix, iy, iz = (int(v) for v in lf)
+        if action[e] == H_REFINE:
+            for c in _children((L, ix, iy, iz)):
+                out[(b,) + c] = (int(p[e]), float(pred_next[e]), e)
+        elif action[e] == P_REFINE:
+            out[(b, L, ix, iy, iz)] = (int(p[e]) + 1, float(pred_next[e]), e)
+        else:
+            out[(b, L, ix, iy, iz)] = (int(p[e]), float(pred_next[e]), e)
+    while True:
+        keys = list(out)
+        pts, src = [], []
+        for k in keys:
+            b, L, ix, iy, iz = k
+            for f in range(6):
+                d, s = divmod(f, 2)
+                xi = -1.0 + (2.0 * np.array([ix, iy, iz], dtype=np.float64) + 1.0) / (1 << L)
+                xi[d] = -1.0 + (2.0 * [ix, iy, iz][d] + (2.0 if s else 0.0)) / (1 << L) + (1e-7 if s else -1e-7)
+                pts.append(block_map(blocks[b], xi[None])[0])
+                src.append(k)
+        where, ref = _locate(blocks, np.array(pts))
+        coarse = set()
+        for k, b2, r in zip(src, where, ref):
+            if b2 < 0:
+                continue
+            L = k[1]
+            for l in range(L, -1, -1):
+                cell = tuple(int(min(max(np.floor((r[i] + 1.0) / 2.0 * (1 << l)), 0), (1 << l) - 1)) for i in range(3))
+                if (int(b2), l) + cell in out:
+                    if l < L - 1:
+                        coarse.add((int(b2), l) + cell)
+                    break
+        if not coarse:
+            return out
+        for k in coarse:
+            pe, _, parent = out.pop(k)
+            for c in _children(k[1:]):
+                out[(k[0],) + c] = (pe, float(pred_init), parent)

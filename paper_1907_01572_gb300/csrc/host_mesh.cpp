@@ -76,6 +76,11 @@ bool across(const BlockTopo& T, int b, int f, int lev, const int idx[3], int& b2
 
 }  // namespace
 
+bool block_face_neighbour(const BlockTopo& T, int b, int f, int lev, const int idx[3], int& b2, int c2[3]) {
+    int f2 = 0, o = 0;
+    return across(T, b, f, lev, idx, b2, f2, o, c2);
+}
+
 bool build_block_topology(const dg_block* blocks, int n_blocks, BlockTopo& topo, std::string& err) {
     topo.n_blocks = n_blocks;
     topo.face.assign(6 * (size_t)n_blocks, BlockFace{});

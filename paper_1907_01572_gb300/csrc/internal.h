@@ -109,6 +109,9 @@ struct LevelHost {
 // Block connectivity from the block maps: faces whose four corners coincide
 // are glued, with the orientation under which the corners match.
 bool build_block_topology(const dg_block* blocks, int n_blocks, BlockTopo& topo, std::string& err);
+// The level-lev cell of block b2 (index c2) across face f of the level-lev cell idx of
+// block b, when f lies on b's boundary; false on the domain boundary.
+bool block_face_neighbour(const BlockTopo& T, int b, int f, int lev, const int idx[3], int& b2, int c2[3]);
 // Builds the finest level's connectivity; returns false with a message on a malformed mesh.
 bool build_level_connectivity(LevelHost& L, const BlockTopo& topo, std::string& err);
 // Coarsens `fine` into `coarse` (Sec. II.E.3); returns false when no family merges.

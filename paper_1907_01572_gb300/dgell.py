@@ -113,6 +113,8 @@ _SIGS = {
     "dg_hp_mark": ([ctypes.c_int, _P, _P, _P, _P, ctypes.POINTER(dg_amr_opts), _P, _P], ctypes.c_int),
     "dg_hp_refine": ([ctypes.c_int, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                       _P, _P, _P, _P], ctypes.c_int),
+    "dg_hp_refine_mesh": ([ctypes.POINTER(dg_mesh_desc), _P, _P, ctypes.c_double, ctypes.c_int,
+                           ctypes.POINTER(ctypes.c_int), _P, _P, _P, _P, _P], ctypes.c_int),
 }
 
 _lib = None
@@ -246,6 +248,31 @@ def hp_refine(leaves, p, action, pred_next, pred_init=float("inf")):
                               L.ctypes.data_as(ctypes.c_void_p), P.ctypes.data_as(ctypes.c_void_p),
                               Q.ctypes.data_as(ctypes.c_void_p), R.ctypes.data_as(ctypes.c_void_p)))
     return L, P, Q, R
+
+
+def hp_refine_mesh(desc, action, pred_next, pred_init=float("inf")):
+    """dg_hp_refine_mesh on an inputs-style mesh dict: returns the refined
+    mesh dict (same domain / blocks) and the arrays (pred, parent)."""
+    d = make_mesh_desc(desc)
+    a, ap = _host(action, np.int32)
+    q, qp = _host(pred_next, np.float64)
+    cnt = ctypes.c_int(0)
+    rc = lib().dg_hp_refine_mesh(ctypes.byref(d), ap, qp, pred_init, 0, ctypes.byref(cnt), None, None, None, None, None)
+    if rc not in (DG_OK, DG_ERR_INVALID) or (rc == DG_ERR_INVALID and cnt.value == 0 and len(a) > 0):
+        _check(rc)
+    m = cnt.value
+    L = np.zeros((m, 4), dtype=np.int32)
+    P = np.zeros(m, dtype=np.int32)
+    B = np.zeros(m, dtype=np.int32)
+    Q = np.zeros(m, dtype=np.float64)
+    R = np.zeros(m, dtype=np.int32)
+    vp = lambda x: x.ctypes.data_as(ctypes.c_void_p)
+    _check(lib().dg_hp_refine_mesh(ctypes.byref(d), ap, qp, pred_init, m, ctypes.byref(cnt), vp(L), vp(P), vp(B),
+                                   vp(Q), vp(R)))
+    out = dict(desc, leaves=L, p=P)
+    if desc.get("blocks"):
+        out["elem_block"] = B
+    return out, Q, R
 
 
 def dg_version():

@@ -36,7 +36,7 @@ def test_binding_covers_the_header():
 
 def test_version_and_error_text(lib):
     from paper_1907_01572_gb300 import dgell
-    assert dgell.lib().dg_version() == 114
+    assert dgell.lib().dg_version() == 115
     assert isinstance(dgell.lib().dg_last_error(), bytes)
 
 

@@ -91,3 +91,45 @@ def test_mark_rejects_bad_theta():
     for crit, th in (('fraction', 0.0), ('fraction', 1.5), ('mean', -1.0), ('mean', math.inf)):
         with pytest.raises(ValueError):
             hpamr.mark(list(eta), crit, th)
+
+
+def _block_dict(out, Q, R):
+    return {(int(b),) + tuple(int(v) for v in lf): (int(pp), float(q), int(r))
+            for b, lf, pp, q, r in zip(out["elem_block"], out["leaves"], out["p"], Q, R)}
+
+
+@pytest.mark.parametrize("case", ["pair5", "pair13", "pair23", "sphere"])
+def test_block_mesh_refinement_matches_oracle(case):
+    """dg_hp_refine_mesh on multi-block meshes (block connectivity and
+    orientation codes) against the oracle's physical point location, over
+    two random refinement steps; the result builds as an oracle block mesh
+    (2:1 across every interface, tiling every block)."""
+    from oracle.blockmesh import BlockMesh
+    if case == "sphere":
+        d = inputs.cubed_sphere_mesh(level=1, a=1.0, r=3.0, r_out=30.0, refine_wedge=(2, 3), pmin=2, pmax=4)
+    else:
+        d = inputs.block_pair_mesh(rot=int(case[4:]), level=1, refine_block=0, seed=1)
+    rng = np.random.default_rng(len(case))
+    for step in range(2):
+        n = len(d["p"])
+        act = rng.choice([0, 0, 0, 1, 2], size=n).astype(np.int32)
+        act[np.asarray(d["p"]) >= 8] = 0
+        nxt = rng.random(n)
+        out, Q, R = dgell.hp_refine_mesh(d, act, nxt, pred_init=math.inf)
+        ref = hpamr.refine_blocks(d["blocks"], d["elem_block"], d["leaves"], d["p"], list(act), list(nxt), math.inf)
+        assert _block_dict(out, Q, R) == ref
+        BlockMesh(d["blocks"], out["elem_block"], out["leaves"], out["p"])
+        d = out
+
+
+def test_refine_mesh_single_box_equals_refine():
+    d = inputs.sweep_mesh(level=1, seed=3)
+    n = len(d["p"])
+    rng = np.random.default_rng(9)
+    act = rng.choice([0, 1, 2], size=n).astype(np.int32)
+    nxt = rng.random(n)
+    out, Q, R = dgell.hp_refine_mesh(d, act, nxt)
+    L, P, Q2, R2 = dgell.hp_refine(d["leaves"], d["p"], act, nxt)
+    assert np.array_equal(out["leaves"], L) and np.array_equal(out["p"], P)
+    assert np.array_equal(Q, Q2) and np.array_equal(R, R2)
+    assert out["lo"] == d["lo"] and out.get("warp") == d.get("warp")

@@ -105,3 +105,29 @@ def test_random_refinement_sequences_stay_balanced(seed):
         p = [out[lf][0] for lf in lv]
         pred = [out[lf][1] for lf in lv]
         assert max(p) <= 4
+
+
+def test_balance_across_a_turned_block_interface_by_hand():
+    """Two unit boxes glued at x = 1, the second turned (rotation 5): the
+    block-0 family next to (1, 0, 0) is at level 2; splitting its four
+    children on the interface puts level-3 cells against the level-1 cell
+    [1, 1.5] x [0, 0.5]^2 of block 1 across the interface and against the
+    level-1 cells (1, 1, 1, 0) and (1, 1, 0, 1) of block 0 itself: those
+    three, and nothing else, must split."""
+    from oracle.blockmesh import BlockMesh, block_map
+    d = inputs.block_pair_mesh(rot=5, level=1, refine_block=0, seed=1)
+    lv, eb, p = np.asarray(d["leaves"]), np.asarray(d["elem_block"]), np.asarray(d["p"])
+    n = len(p)
+    act = [H if (eb[e] == 0 and lv[e][0] == 2 and lv[e][1] == 3) else N for e in range(n)]
+    assert act.count(H) == 4
+    out = hpamr.refine_blocks(d["blocks"], eb, lv, p, act, [1.0] * n, pred_init=math.inf)
+    split = [k for k in out if k[0] == 1 and k[1] == 2]
+    assert len(split) == 8
+    for k in split:
+        c = block_map(d["blocks"][1], (-1.0 + (2.0 * np.array(k[2:]) + 1.0) / 4.0)[None])[0]
+        assert 1.0 < c[0] < 1.5 and 0.0 < c[1] < 0.5 and 0.0 < c[2] < 0.5
+        assert out[k][1] == math.inf
+    assert (0, 1, 1, 1, 0) not in out and (0, 1, 1, 0, 1) not in out
+    assert len(out) == n - 4 + 32 - 3 + 24
+    keys = sorted(out)
+    BlockMesh(d["blocks"], [k[0] for k in keys], [k[1:] for k in keys], [out[k][0] for k in keys])
