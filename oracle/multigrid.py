@@ -23,6 +23,10 @@ Readings:
    lambda_max = max_k lambda_k.  CG stops early when p.Jp <= 0 or r.r = 0;
    a smoother whose estimate stayed 0 skips its Chebyshev steps.
  * Level 0 "solve": the smoother (paper) or an exact dense Cholesky solve.
+ * Coarse operators: re-discretised per level (paper); as an option the
+   Galerkin products P^T J P (not in the paper), which keep the V-cycle
+   contracting on the compactified cubed sphere where re-discretised levels
+   do not (tests/test_oracle_multigrid.py).
 
 Pins: Chebyshev error polynomial on a diagonal matrix, Gershgorin bound >=
 lambda_max, CG iterates vs textbook CG, prolongation exactness on coarse
@@ -244,18 +248,58 @@ def schwarz_smoother(A, inv_blocks, dof_off, x, b, n_cycles=3, omega=0.7):
     return x
 
 
-class Hierarchy:
-    """Level operators J_l and prolongations for the V-cycle of Alg. 3."""
+def uniform_block_levels(blocks, level, p):
+    """Level meshes 0..level of a multi-block mesh refined uniformly (every
+    block at the same level, degree p everywhere) and their family groups,
+    for Hierarchy(levels=...)."""
+    from .blockmesh import BlockMesh
+    meshes, groups = [], []
+    for L in range(level + 1):
+        m = 1 << L
+        lv = [(L, i, j, k) for k in range(m) for j in range(m) for i in range(m)]
+        eb = [b for b in range(len(blocks)) for _ in lv]
+        leaves = [tuple(lf) for _ in blocks for lf in lv]
+        meshes.append(BlockMesh(blocks, eb, leaves, [p] * len(leaves)))
+    for L in range(level):
+        fine, coarse = meshes[L + 1], meshes[L]
+        fkey = {(int(b),) + tuple(int(v) for v in lf): e for e, (b, lf) in enumerate(zip(fine.elem_block, fine.leaves))}
+        grp = []
+        for b, lf in zip(coarse.elem_block, coarse.leaves):
+            l, i, j, k = (int(v) for v in lf)
+            grp.append([(fkey[(int(b), l + 1, 2 * i + (c & 1), 2 * j + ((c >> 1) & 1), 2 * k + ((c >> 2) & 1))],
+                         (c & 1, (c >> 1) & 1, (c >> 2) & 1)) for c in range(8)])
+        groups.append(grp)
+    return meshes, groups
 
-    def __init__(self, mesh, C=10.0, coef=None, extra=0):
+
+class Hierarchy:
+    """Level operators J_l and prolongations for the V-cycle of Alg. 3.
+
+    coarse_ops='rediscretised' (the paper: the SIPG operator assembled on
+    every level mesh) or 'galerkin' (every coarse operator P^T J P from the
+    next finer one); levels=(meshes, groups) gives the level meshes directly
+    (e.g. uniform_block_levels) instead of coarsening a single-box mesh."""
+
+    def __init__(self, mesh, C=10.0, coef=None, extra=0, coarse_ops='rediscretised', levels=None):
         from . import sipg
-        self.meshes, self.groups = hierarchy(mesh)
+        if levels is None:
+            self.meshes, self.groups = hierarchy(mesh)
+        else:
+            self.meshes, self.groups = list(levels[0]), list(levels[1])
         self.P = [prolongation(self.meshes[l + 1], self.meshes[l], self.groups[l])
                   for l in range(len(self.meshes) - 1)]
-        self.L = [sipg.assemble(m, C, extra) for m in self.meshes]
+        if coarse_ops == 'galerkin':
+            self.L = [None] * len(self.meshes)
+            self.L[-1] = sipg.assemble(self.meshes[-1], C, extra)
+            for l in range(len(self.meshes) - 2, -1, -1):
+                self.L[l] = (self.P[l].T @ self.L[l + 1] @ self.P[l]).tocsr()
+        elif coarse_ops == 'rediscretised':
+            self.L = [sipg.assemble(m, C, extra) for m in self.meshes]
+        else:
+            raise ValueError("coarse_ops is 'rediscretised' or 'galerkin'")
         self.J = list(self.L)
         if coef is not None:
-            O = sipg.assemble(mesh, C, extra, coef) - self.L[-1]
+            O = sipg.assemble(self.meshes[-1], C, extra, coef) - self.L[-1]
             self.O = [None] * len(self.meshes)
             self.O[-1] = O
             for l in range(len(self.meshes) - 2, -1, -1):

@@ -163,3 +163,26 @@ def test_element_schwarz_smoother():
     f = inputs.random_vector(m.n_dofs, seed=3)
     u, its, hist = krylov.fcg(L, f, precond=lambda r: H.vcycle(r, smoother_kind="schwarz"), tol=1e-10, max_iter=100)
     assert np.linalg.norm(f - L @ u) <= 1e-10 * np.linalg.norm(f) and its < 80
+
+
+def test_galerkin_coarse_operators_on_the_compactified_sphere():
+    """13-block cubed sphere with the inverse-radius shell to r = 1e9 (level
+    1, p = 3, two levels, exact coarse solve): with element-Schwarz
+    smoothing, Galerkin coarse operators P^T J P make MG-FCG reach 1e-10,
+    the re-discretised coarse level does not within the same 150 iterations.
+    The Galerkin operators satisfy their definition exactly."""
+    from oracle import krylov, multigrid
+    from paper_1907_01572_gb300 import inputs
+    levels = multigrid.uniform_block_levels(inputs.cubed_sphere_blocks(a=2.0, r=10.0, r_out=1e9), 1, 3)
+    b = np.random.default_rng(0).standard_normal(levels[0][-1].n_dofs)
+    its = {}
+    for ops in ("galerkin", "rediscretised"):
+        H = multigrid.Hierarchy(None, levels=levels, coarse_ops=ops)
+        x, it, hist = krylov.fcg(H.J[-1], b, precond=lambda r: H.vcycle(r, coarse='cholesky', smoother_kind='schwarz'),
+                                 tol=1e-10, max_iter=150)
+        its[ops] = (it, hist[-1])
+        if ops == "galerkin":
+            G = (H.P[0].T @ H.J[1] @ H.P[0]).toarray()
+            assert np.abs(H.J[0].toarray() - G).max() <= 1e-12 * np.abs(G).max()
+    assert its["galerkin"][1] < 1e-10 and its["galerkin"][0] < 150, its
+    assert its["rediscretised"][1] > 1e-9, its
