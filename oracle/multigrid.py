@@ -23,6 +23,14 @@ Readings:
    lambda_max = max_k lambda_k.  CG stops early when p.Jp <= 0 or r.r = 0;
    a smoother whose estimate stayed 0 skips its Chebyshev steps.
  * Level 0 "solve": the smoother (paper) or an exact dense Cholesky solve.
+ * Overlapping Schwarz subdomains (Alg. 6, eq. schwarz_weight), for meshes of
+   one degree with conforming faces: the node layers of the touching
+   elements; xi_ext beyond e_c's boundary = the coinciding e_c coordinate
+   moved outward by the neighbour node's LGL distance from the contact;
+   delta = the overlap width in xi_ext; local problems solved exactly (the
+   paper uses CG to 1e-3).  At the domain boundary and where three or five
+   blocks meet along an edge the weights do not sum to one, as the
+   construction implies.
  * Coarse operators: re-discretised per level (paper); as an option the
    Galerkin products P^T J P (not in the paper), which keep the V-cycle
    contracting on the compactified cubed sphere where re-discretised levels
@@ -248,6 +256,108 @@ def schwarz_smoother(A, inv_blocks, dof_off, x, b, n_cycles=3, omega=0.7):
     return x
 
 
+def schwarz_phi(t):
+    """phi of the Schwarz weight (eq. schwarz_weight): sgn(t) for |t| > 1,
+    (15 t - 10 t^3 + 3 t^5) / 8 inside."""
+    t = np.asarray(t, dtype=np.float64)
+    return np.where(np.abs(t) > 1.0, np.sign(t), (15.0 * t - 10.0 * t ** 3 + 3.0 * t ** 5) / 8.0)
+
+
+def schwarz_weight(xi_ext, delta):
+    """w_h(xi_ext) = (phi((xi_ext + 1) / delta) - phi((xi_ext - 1) / delta)) / 2
+    (eq. schwarz_weight)."""
+    return 0.5 * (schwarz_phi((np.asarray(xi_ext) + 1.0) / delta) - schwarz_phi((np.asarray(xi_ext) - 1.0) / delta))
+
+
+def overlap_subdomains(mesh, n_overlap=2):
+    """Element-centred Schwarz subdomains with overlap (Sec. II.E.5) for a
+    mesh whose elements all have the same degree and meet conformingly
+    (any block layout).  Subdomain of e_c: its own nodes, the nodes of every
+    element touching it that coincide with e_c's boundary nodes (faces,
+    edges, corners), and the nodes of those elements within n_overlap - 1
+    further index layers of them.  Each node gets its extended LGL
+    coordinate xi_ext in e_c's frame -- its own LGL coordinate on e_c, and
+    beyond e_c's boundary the coinciding e_c coordinate moved outward by the
+    node's LGL distance from the contact (the direction found from the
+    neighbour's node positions and e_c's Jacobian) -- and the weight
+    W = prod_i w_h(xi_ext^i) with delta the overlap width in xi_ext.
+    Returns [(global dofs, weights)] per element."""
+    from scipy.spatial import cKDTree
+    n = int(mesh.n[0])
+    if np.any(mesh.n != n):
+        raise ValueError("overlap_subdomains: one degree for every element")
+    n3 = n ** 3
+    xl, _ = tables.lgl_nodes_weights(n)
+    X = np.vstack([mesh.node_coords(e) for e in range(mesh.n_elems)])
+    tree = cKDTree(X)
+    idx3 = np.array([(a, b, c) for c in range(n) for b in range(n) for a in range(n)])
+    lin = lambda q: int(q[0] + n * q[1] + n * n * q[2])
+    bnd = [k for k in range(n3) if (idx3[k] == 0).any() or (idx3[k] == n - 1).any()]
+    subs = []
+    for e in range(mesh.n_elems):
+        o = int(mesh.dof_off[e])
+        contact = {}
+        for k in bnd:
+            for j in tree.query_ball_point(X[o + k], 1e-9 * max(1.0, np.linalg.norm(X[o + k]))):
+                if not (o <= j < o + n3):
+                    contact[j] = k
+        by_elem = {}
+        for j, k in contact.items():
+            e2 = int(np.searchsorted(mesh.dof_off, j, side='right') - 1)
+            by_elem.setdefault(e2, {})[j - int(mesh.dof_off[e2])] = k
+        dofs = list(range(o, o + n3))
+        xis = list(tables.tensor_points(xl))
+        for e2 in sorted(by_elem):
+            cmap = by_elem[e2]
+            o2 = int(mesh.dof_off[e2])
+            C = idx3[np.array(sorted(cmap))]
+            pinned = [a for a in range(3) if len(set(C[:, a])) == 1]
+            for q in range(n3):
+                qi = idx3[q]
+                if np.abs(C - qi[None]).max(axis=1).min() > n_overlap - 1:
+                    continue
+                c = qi.copy()
+                for a in pinned:
+                    c[a] = C[0, a]
+                xi = xl[idx3[cmap[lin(c)]]].astype(np.float64)
+                for a in pinned:
+                    if qi[a] == c[a]:
+                        continue
+                    nxt = c.copy()
+                    nxt[a] += 1 if qi[a] > c[a] else -1
+                    dxi = np.linalg.solve(mesh.jacobian_at(e, xi[None])[0], X[o2 + lin(nxt)] - X[o2 + lin(c)])
+                    ax = int(np.argmax(np.abs(dxi)))
+                    xi[ax] += np.sign(dxi[ax]) * abs(xl[qi[a]] - xl[c[a]])
+                dofs.append(o2 + q)
+                xis.append(xi)
+        xis = np.array(xis)
+        delta = max(float(np.abs(xis).max()) - 1.0, 1e-12)
+        subs.append((np.array(dofs, dtype=np.int64), np.prod(schwarz_weight(xis, delta), axis=1)))
+    return subs
+
+
+def overlap_schwarz_smoother(A, subs, x, b, n_cycles=3, factors=None):
+    """Alg. 6 with overlapping subdomains: n_cycles times r = b - A x, then
+    x += sum_s R_s^T W_s dx_s with R_s A R_s^T dx_s = R_s r solved exactly
+    (Cholesky; factors from overlap_factors may be passed in)."""
+    Ad = A.tocsr()
+    if factors is None:
+        factors = overlap_factors(Ad, subs)
+    x = x.copy()
+    for _ in range(n_cycles):
+        r = b - Ad @ x
+        dx = np.zeros_like(x)
+        for (d, W), f in zip(subs, factors):
+            np.add.at(dx, d, W * sla.cho_solve(f, r[d]))
+        x = x + dx
+    return x
+
+
+def overlap_factors(A, subs):
+    Ad = A.tocsr()
+    return [sla.cho_factor(Ad[d][:, d].toarray()) for d, _ in subs]
+
+
 def uniform_block_levels(blocks, level, p):
     """Level meshes 0..level of a multi-block mesh refined uniformly (every
     block at the same level, degree p everywhere) and their family groups,
@@ -317,17 +427,26 @@ class Hierarchy:
         return sla.cho_solve(self._chol, f)
 
     def vcycle(self, f, n_eigs=15, n_cheb=15, Lam=20.0, coarse='smoother', smoother_kind='chebyshev',
-               n_schwarz=3, omega=0.7):
+               n_schwarz=3, omega=0.7, n_overlap=2):
         """Alg. 3 with the level meshes fixed in advance; smoother_kind
-        'chebyshev' (Alg. 4 with Alg. 5) or 'schwarz' (element subdomains,
-        exact local solves)."""
+        'chebyshev' (Alg. 4 with Alg. 5), 'schwarz' (element subdomains,
+        exact local solves) or 'schwarz_overlap' (Alg. 6 with overlapping
+        subdomains and the weights w_h, exact local solves)."""
         Lt = self.n_levels - 1
         if smoother_kind == 'schwarz' and not hasattr(self, '_sinv'):
             self._sinv = [schwarz_blocks(self.J[l], self.meshes[l].dof_off) for l in range(Lt + 1)]
+        if smoother_kind == 'schwarz_overlap' and not hasattr(self, '_ovl'):
+            self._ovl = []
+            for l in range(Lt + 1):
+                subs = overlap_subdomains(self.meshes[l], n_overlap)
+                self._ovl.append((subs, overlap_factors(self.J[l], subs)))
 
         def smooth(l, v, b):
             if smoother_kind == 'schwarz':
                 return schwarz_smoother(self.J[l], self._sinv[l], self.meshes[l].dof_off, v, b, n_schwarz, omega)
+            if smoother_kind == 'schwarz_overlap':
+                subs, fac = self._ovl[l]
+                return overlap_schwarz_smoother(self.J[l], subs, v, b, n_schwarz, fac)
             return smoother(self.J[l], v, b, n_eigs, n_cheb, Lam)[0]
 
         fs = [None] * (Lt + 1)
