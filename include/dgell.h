@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define DGELL_VERSION 115
+#define DGELL_VERSION 116
 
 enum {
     DG_OK = 0,
@@ -56,6 +56,12 @@ typedef enum {
     DG_MAP_AFFINE = 0,      /* block map = identity on the box [lo, hi]^3 */
     DG_MAP_SINE_WARP = 1    /* x_i += a sin(2 pi k_i x_i) sin(2 pi k_{i+1} x_{i+1}), cyclic i */
 } dg_map_kind;
+
+/* Boundary condition of a block face on the domain boundary (Sec. II.A.2,
+ * eqs. DirichletBC, NeumannBC, RobinBC).  This version implements Dirichlet
+ * data only: a mesh with a Neumann or Robin tag on a boundary face is
+ * rejected by dg_mesh_create with DG_ERR_UNSUPPORTED. */
+typedef enum { DG_BC_DIRICHLET = 0, DG_BC_NEUMANN = 1, DG_BC_ROBIN = 2 } dg_bc_kind;
 
 typedef enum {
     DG_BLOCK_HEX8 = 0,      /* trilinear map through 8 corners (a box or any parallelepiped) */
@@ -103,7 +109,16 @@ typedef struct {
     int n_blocks;          /* 0: single box */
     const dg_block* blocks;    /* host, n_blocks */
     const int* elem_block;     /* host, n_elems */
+    const int* bc;             /* host, 6 per block (6 for the single box), face 2 d + (s > 0):
+                                  the dg_bc_kind of that block face where it lies on the domain
+                                  boundary (ignored on faces glued to another block); NULL: all
+                                  Dirichlet */
 } dg_mesh_desc;
+
+/* A validated mesh: the description's copy with its multigrid hierarchy
+ * (Sec. II.E.3) and block connectivity, built on the host.  Contexts and
+ * footprint queries take it; it may be destroyed once they are made. */
+typedef struct dg_mesh dg_mesh;
 
 /* Discretisation options.  penalty_c is C of eq. (penaltyparameter),
  * sigma = C p_m^2 / h_m; <= 0 selects the default 10. */
@@ -131,17 +146,27 @@ typedef struct {
 int dg_version(void);
 const char* dg_last_error(void);
 
-/* Builds the mesh hierarchy (Sec. II.E.3: surrogate coarsening + 2:1
- * rebalancing, coarse degree = min over children), mortar tables, the 1-D
- * operator tables and all geometry (eqs. Jacobian, Surface-Jacobian, the
- * normal, eq. penaltyparameter) on the device.  stream: a cudaStream_t
- * (NULL = legacy default stream).  Synchronises the stream before return. */
-int dg_ctx_create(const dg_mesh_desc* mesh, const dg_disc_opts* opts, void* stream, dg_ctx** out);
+/* Validates a mesh description (Sec. II.A.1: octree leaves tiling every
+ * block, 2:1 across faces and block interfaces, degrees 1..8, block maps;
+ * boundary tags) and builds, on the host, its block connectivity and its
+ * multigrid hierarchy (Sec. II.E.3: surrogate coarsening + 2:1 rebalancing,
+ * coarse degree = min over children).  The library copies every array of
+ * desc.  Errors: DG_ERR_INVALID (malformed description), DG_ERR_UNSUPPORTED
+ * (a Neumann or Robin tag on a boundary face).  No device work. */
+int dg_mesh_create(const dg_mesh_desc* desc, dg_mesh** out);
+void dg_mesh_destroy(dg_mesh* mesh);
+
+/* Uploads a mesh: mortar tables, the 1-D operator tables and all geometry
+ * (eqs. Jacobian, Surface-Jacobian, the normal, eq. penaltyparameter) on the
+ * device, for every level of the mesh's hierarchy.  The context keeps its own
+ * copy of what it needs from mesh.  stream: a cudaStream_t (NULL = legacy
+ * default stream).  Synchronises the stream before return. */
+int dg_ctx_create(const dg_mesh* mesh, const dg_disc_opts* opts, void* stream, dg_ctx** out);
 void dg_ctx_destroy(dg_ctx* ctx);
 
 /* Device bytes dg_ctx_create would hold for this mesh (admission control);
  * host-only, no device work. */
-int dg_ctx_footprint(const dg_mesh_desc* mesh, const dg_disc_opts* opts, size_t* bytes);
+int dg_ctx_footprint(const dg_mesh* mesh, const dg_disc_opts* opts, size_t* bytes);
 
 int dg_level_info_get(dg_ctx* ctx, int level, dg_level_info* info);
 
@@ -190,6 +215,9 @@ typedef struct {
     double lam_scale;  /* the Chebyshev interval uses lam_scale x the CG estimate of lambda_max
                           (a safety factor against an underestimate on strongly stretched
                           meshes); <= 0 -> 1, the paper's Alg. 4 */
+    double lam_fixed;  /* > 0: no CG steps; the Chebyshev steps use lambda_max = lam_fixed on
+                          every level (a linear smoother, Alg. 4 with a given bound instead of
+                          Alg. 5's estimate); <= 0 -> the CG estimate (the paper) */
 } dg_cheb_opts;
 
 int dg_smooth(dg_ctx* ctx, int level, int prec, const void* b, void* x,

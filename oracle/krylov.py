@@ -5,21 +5,26 @@ tol ||b||_2 (the printed loop condition joins the two tests with "or", which
 never stops when the iteration cap is reached); the preconditioner is
 applied to r_k.
 
-Pins: with the identity preconditioner the iterates equal textbook CG; the
-multigrid-preconditioned solve reaches 1e-10 relative residual on the
-Poisson problem (tests/test_oracle_multigrid.py).
+Pins (tests/test_oracle_multigrid.py): with the identity preconditioner every
+iterate equals textbook CG's, and with a fixed SPD preconditioner M every
+iterate equals textbook preconditioned CG's (in exact arithmetic FCG(1) with
+a linear preconditioner is PCG); the multigrid-preconditioned solve reaches
+1e-10 relative residual on the Poisson problem.
 """
 import numpy as np
 
 
-def fcg(A, b, x0=None, precond=None, tol=1e-10, max_iter=200):
-    """Returns (x, iterations, history of ||r_k|| / ||b||)."""
+def fcg(A, b, x0=None, precond=None, tol=1e-10, max_iter=200, callback=None):
+    """Returns (x, iterations, history of ||r_k|| / ||b||).  callback(k, x_k),
+    if given, sees every iterate (k = 0 is the initial guess)."""
     x = np.zeros_like(b) if x0 is None else x0.copy()
     r = b - A @ x
     nb = np.linalg.norm(b)
     if nb == 0.0:
         return x, 0, [0.0]
     hist = [np.linalg.norm(r) / nb]
+    if callback is not None:
+        callback(0, x)
     k = 0
     d = q = None
     rho = None
@@ -40,4 +45,6 @@ def fcg(A, b, x0=None, precond=None, tol=1e-10, max_iter=200):
         rho = rho_k
         k += 1
         hist.append(np.linalg.norm(r) / nb)
+        if callback is not None:
+            callback(k, x)
     return x, k, hist

@@ -39,6 +39,13 @@ Readings:
 Pins: Chebyshev error polynomial on a diagonal matrix, Gershgorin bound >=
 lambda_max, CG iterates vs textbook CG, prolongation exactness on coarse
 polynomials, restriction/Galerkin identities (tests/test_oracle_multigrid.py);
+the V-cycle with a fixed-lambda (linear) Chebyshev smoother equals its
+closed form built from explicit matrices -- smoother S(x, b) = R x + (I - R)
+J^-1 b with the Chebyshev error matrix R = T_k(Z) / T_k(d / c), Z = (d - J) / c
+-- on two and three levels, and planted mistakes (no post-smoothing, f
+restricted instead of f - J v, no "+ v_l") fail that comparison; the CG
+tridiagonal of Alg. 5 equals the one of an independent Lanczos run, and a
+planted beta in place of sqrt(beta) / alpha fails (tests/test_oracle_pins.py);
 element Schwarz: exact in one undamped cycle on a block-diagonal matrix, the
 spectrum of A_ee^-1 A inside (0, 2), MG-FCG with it reaching 1e-10.
 """
@@ -169,9 +176,10 @@ def prolongation(fine, coarse, groups):
     return P
 
 
-def cgeigs(A, x, b, n_iter):
+def cgeigs(A, x, b, n_iter, trace=None):
     """Alg. 5: n_iter CG steps from x with the Gershgorin bound of the
-    Lanczos tridiagonal.  Returns (lambda_max, x)."""
+    Lanczos tridiagonal.  Returns (lambda_max, x).  trace, if a list, receives
+    (T_kk, |T_k,k+1|, lambda_k) of every step k."""
     x = x.copy()
     r = b - A @ x
     p = r.copy()
@@ -197,6 +205,8 @@ def cgeigs(A, x, b, n_iter):
             left = np.sqrt(b_prev) / a_prev
         right = np.sqrt(beta) / a
         lam = max(lam, diag + left + right)
+        if trace is not None:
+            trace.append((diag, right, diag + left + right))
         a_prev, b_prev = a, beta
     return lam, x
 
@@ -426,12 +436,31 @@ class Hierarchy:
             self._chol = sla.cho_factor(self.J[0].toarray())
         return sla.cho_solve(self._chol, f)
 
+    def residual(self, l, f, v):
+        """f - J_l v on level l."""
+        return f - self.J[l] @ v
+
+    def restrict(self, l, r):
+        """(I_h^H)^T r from level l to level l - 1 (eq. temp-G)."""
+        return self.P[l - 1].T @ r
+
+    def prolong(self, l, v):
+        """I_h^H v from level l - 1 to level l (eq. psi-interpolation)."""
+        return self.P[l - 1] @ v
+
+    def coarse_correction(self, l, v, v_coarse):
+        """The smoothed v_l plus the prolonged coarse solution (Alg. 3, on the
+        way up)."""
+        return self.prolong(l, v_coarse) + v
+
     def vcycle(self, f, n_eigs=15, n_cheb=15, Lam=20.0, coarse='smoother', smoother_kind='chebyshev',
-               n_schwarz=3, omega=0.7, n_overlap=2):
+               n_schwarz=3, omega=0.7, n_overlap=2, lam_fixed=None):
         """Alg. 3 with the level meshes fixed in advance; smoother_kind
         'chebyshev' (Alg. 4 with Alg. 5), 'schwarz' (element subdomains,
         exact local solves) or 'schwarz_overlap' (Alg. 6 with overlapping
-        subdomains and the weights w_h, exact local solves)."""
+        subdomains and the weights w_h, exact local solves).  lam_fixed (a
+        number, or one per level, coarsest first): Chebyshev steps on
+        [lam / Lam, lam] with that lam and no CG steps -- a linear smoother."""
         Lt = self.n_levels - 1
         if smoother_kind == 'schwarz' and not hasattr(self, '_sinv'):
             self._sinv = [schwarz_blocks(self.J[l], self.meshes[l].dof_off) for l in range(Lt + 1)]
@@ -447,6 +476,9 @@ class Hierarchy:
             if smoother_kind == 'schwarz_overlap':
                 subs, fac = self._ovl[l]
                 return overlap_schwarz_smoother(self.J[l], subs, v, b, n_schwarz, fac)
+            if lam_fixed is not None:
+                lam = lam_fixed[l] if np.ndim(lam_fixed) else lam_fixed
+                return chebyshev(self.J[l], v, b, lam, Lam, n_cheb)
             return smoother(self.J[l], v, b, n_eigs, n_cheb, Lam)[0]
 
         fs = [None] * (Lt + 1)
@@ -455,12 +487,12 @@ class Hierarchy:
         for l in range(Lt, 0, -1):
             v = smooth(l, np.zeros_like(fs[l]), fs[l])
             vs[l] = v
-            fs[l - 1] = self.P[l - 1].T @ (fs[l] - self.J[l] @ v)
+            fs[l - 1] = self.restrict(l, self.residual(l, fs[l], v))
         if coarse == 'cholesky':
             vs[0] = self.coarse_cholesky(fs[0])
         else:
             vs[0] = smooth(0, np.zeros_like(fs[0]), fs[0])
         for l in range(1, Lt + 1):
-            v = self.P[l - 1] @ vs[l - 1] + vs[l]
+            v = self.coarse_correction(l, vs[l], vs[l - 1])
             vs[l] = smooth(l, v, fs[l])
         return vs[Lt]

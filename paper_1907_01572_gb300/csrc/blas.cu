@@ -215,11 +215,13 @@ __global__ void cg_p_kernel(const SmState* s, T* p, const T* r, long long n) {
         p[i] = r[i] + b * p[i];
 }
 
-// Chebyshev coefficients of Alg. 4 on [lmax/Lambda, lmax], lmax = scale x lam:
+// Chebyshev coefficients of Alg. 4 on [lmax/Lambda, lmax], lmax = scale x lam
+// (or lmax = fixed, which also becomes the reported lam, when fixed > 0):
 // alpha_1 = 1/d, alpha_2 = 2d/(2d^2 - c^2), alpha_k = 1/(d - alpha_{k-1} c^2/4),
 // beta_k = alpha_k d - 1, with the update p <- alpha r + beta p.
-__global__ void sm_cheb_kernel(SmState* s, int n_cheb, double Lambda, double scale) {
-    const double lmax = s->lam * scale;
+__global__ void sm_cheb_kernel(SmState* s, int n_cheb, double Lambda, double scale, double fixed) {
+    if (fixed > 0.0) s->lam = fixed;
+    const double lmax = fixed > 0.0 ? fixed : s->lam * scale;
     if (!(lmax > 0.0) || !isfinite(lmax)) {
         s->skip = 1;
         return;
@@ -450,8 +452,8 @@ cudaError_t cg_p_update(const SmState* s, T* p, const T* r, long long n, cudaStr
 template cudaError_t cg_p_update<double>(const SmState*, double*, const double*, long long, cudaStream_t);
 template cudaError_t cg_p_update<float>(const SmState*, float*, const float*, long long, cudaStream_t);
 
-cudaError_t sm_cheb_coeffs(SmState* s, int n_cheb, double Lambda, double scale, cudaStream_t st) {
-    sm_cheb_kernel<<<1, 1, 0, st>>>(s, n_cheb, Lambda, scale);
+cudaError_t sm_cheb_coeffs(SmState* s, int n_cheb, double Lambda, double scale, double fixed, cudaStream_t st) {
+    sm_cheb_kernel<<<1, 1, 0, st>>>(s, n_cheb, Lambda, scale, fixed);
     return cudaGetLastError();
 }
 template <typename T>

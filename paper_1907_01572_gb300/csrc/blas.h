@@ -54,7 +54,7 @@ cudaError_t sm_beta(SmState* s, const double* rr_new, cudaStream_t st);
 template <typename T>
 cudaError_t cg_p_update(const SmState* s, T* p, const T* r, long long n, cudaStream_t st);
 // Chebyshev
-cudaError_t sm_cheb_coeffs(SmState* s, int n_cheb, double Lambda, double scale, cudaStream_t st);
+cudaError_t sm_cheb_coeffs(SmState* s, int n_cheb, double Lambda, double scale, double fixed, cudaStream_t st);
 template <typename T>
 cudaError_t cheb_step(const SmState* s, int k, const T* b, const T* Ax, T* p, T* x, long long n, cudaStream_t st);
 

@@ -46,6 +46,64 @@ void apply_streams_destroy(ApplyStreams& as) {
         if (as.side[i]) cudaStreamDestroy(as.side[i]);
     as = ApplyStreams{};
 }
+
+template <>
+LevelView<double> level_view<double>(dg_ctx* c, int l) {
+    LevelDev& L = c->lv[l];
+    LevelView<double> v{};
+    v.n_elems = L.h.n_elems();
+    v.p = L.p;
+    v.dof_off = L.dof_off;
+    v.vqp_off = L.vqp_off;
+    v.G = L.G64;
+    v.c0 = L.z_active ? L.c0_64 : nullptr;
+    v.Ob = L.z_active ? L.Ob64 : nullptr;
+    v.Ob_off = L.Ob_off;
+    v.slot_off = L.slot_off;
+    v.slot_mortar = L.slot_mortar;
+    v.slot_face = L.slot_face;
+    v.slot_side = L.slot_side;
+    v.mortars = L.mortars;
+    v.mg = L.mg64;
+    v.sigma = L.sigma64;
+    v.tab = c->tab64;
+    v.ftab = c->ftab64;
+    v.ft = c->ft;
+    v.ob_total = (long long)L.ob_count;
+    v.oriented = L.oriented;
+    v.chk = device_check_flag();
+    v.mt = L.mt64;
+    return v;
+}
+
+template <>
+LevelView<float> level_view<float>(dg_ctx* c, int l) {
+    LevelDev& L = c->lv[l];
+    LevelView<float> v{};
+    v.n_elems = L.h.n_elems();
+    v.p = L.p;
+    v.dof_off = L.dof_off;
+    v.vqp_off = L.vqp_off;
+    v.G = L.G32;
+    v.c0 = L.z_active ? L.c0_32 : nullptr;
+    v.Ob = L.z_active ? L.Ob32 : nullptr;
+    v.Ob_off = L.Ob_off;
+    v.slot_off = L.slot_off;
+    v.slot_mortar = L.slot_mortar;
+    v.slot_face = L.slot_face;
+    v.slot_side = L.slot_side;
+    v.mortars = L.mortars;
+    v.mg = L.mg32;
+    v.sigma = L.sigma32;
+    v.tab = c->tab32;
+    v.ftab = c->ftab32;
+    v.ft = c->ft;
+    v.ob_total = (long long)L.ob_count;
+    v.oriented = L.oriented;
+    v.chk = device_check_flag();
+    v.mt = L.mt32;
+    return v;
+}
 }  // namespace dg
 
 namespace {
@@ -75,64 +133,8 @@ int resolve_level(dg_ctx* c, int level) {
 }
 
 template <typename T>
-LevelView<T> view(dg_ctx* c, int l);
-
-template <>
-LevelView<double> view<double>(dg_ctx* c, int l) {
-    LevelDev& L = c->lv[l];
-    LevelView<double> v{};
-    v.n_elems = L.h.n_elems();
-    v.p = L.p;
-    v.dof_off = L.dof_off;
-    v.vqp_off = L.vqp_off;
-    v.G = L.G64;
-    v.c0 = L.z_active ? L.c0_64 : nullptr;
-    v.Ob = L.z_active ? L.Ob64 : nullptr;
-    v.Ob_off = L.Ob_off;
-    v.slot_off = L.slot_off;
-    v.slot_mortar = L.slot_mortar;
-    v.slot_face = L.slot_face;
-    v.slot_side = L.slot_side;
-    v.mortars = L.mortars;
-    v.mg = L.mg64;
-    v.sigma = L.sigma64;
-    v.tab = c->tab64;
-    v.ftab = c->ftab64;
-    v.ft = c->ft;
-    v.ob_total = (long long)L.ob_count;
-    v.oriented = L.oriented;
-    v.chk = device_check_flag();
-    v.mt = L.mt64;
-    return v;
-}
-
-template <>
-LevelView<float> view<float>(dg_ctx* c, int l) {
-    LevelDev& L = c->lv[l];
-    LevelView<float> v{};
-    v.n_elems = L.h.n_elems();
-    v.p = L.p;
-    v.dof_off = L.dof_off;
-    v.vqp_off = L.vqp_off;
-    v.G = L.G32;
-    v.c0 = L.z_active ? L.c0_32 : nullptr;
-    v.Ob = L.z_active ? L.Ob32 : nullptr;
-    v.Ob_off = L.Ob_off;
-    v.slot_off = L.slot_off;
-    v.slot_mortar = L.slot_mortar;
-    v.slot_face = L.slot_face;
-    v.slot_side = L.slot_side;
-    v.mortars = L.mortars;
-    v.mg = L.mg32;
-    v.sigma = L.sigma32;
-    v.tab = c->tab32;
-    v.ftab = c->ftab32;
-    v.ft = c->ft;
-    v.ob_total = (long long)L.ob_count;
-    v.oriented = L.oriented;
-    v.chk = device_check_flag();
-    v.mt = L.mt32;
-    return v;
+LevelView<T> view(dg_ctx* c, int l) {
+    return level_view<T>(c, l);
 }
 
 template <typename T>
@@ -239,8 +241,9 @@ int ensure_work(dg_ctx* c, int l) {
     return DG_OK;
 }
 
-void cheb_defaults(const dg_cheb_opts* o, int& ne, int& nc, double& Lam, double& scale) {
-    ne = (o && o->n_eigs > 0) ? o->n_eigs : 15;
+void cheb_defaults(const dg_cheb_opts* o, int& ne, int& nc, double& Lam, double& scale, double& fixed) {
+    fixed = (o && o->lam_fixed > 0) ? o->lam_fixed : 0.0;
+    ne = fixed > 0 ? 0 : ((o && o->n_eigs > 0) ? o->n_eigs : 15);
     nc = (o && o->n_cheb > 0) ? o->n_cheb : 15;
     Lam = (o && o->Lambda > 0) ? o->Lambda : 20.0;
     scale = (o && o->lam_scale > 0) ? o->lam_scale : 1.0;
@@ -254,8 +257,8 @@ int smooth_t(dg_ctx* c, int l, const T* b, T* x, const dg_cheb_opts* o) {
     if (rc) return rc;
     if ((rc = ensure_dense(c, l))) return rc;
     int ne, nc;
-    double Lam, scale;
-    cheb_defaults(o, ne, nc, Lam, scale);
+    double Lam, scale, fixed;
+    cheb_defaults(o, ne, nc, Lam, scale, fixed);
     Work<T>& W = work_of<T>(c->lv[l]);
     const long long n = c->lv[l].h.n_dofs();
     cudaStream_t st = c->st;
@@ -270,7 +273,7 @@ int smooth_t(dg_ctx* c, int l, const T* b, T* x, const dg_cheb_opts* o) {
         CK(cg_p_update<T>(W.sm, W.p, W.r, n, st));
         c->launches += 3;
     }
-    CK(sm_cheb_coeffs(W.sm, nc, Lam, scale, st));
+    CK(sm_cheb_coeffs(W.sm, nc, Lam, scale, fixed, st));
     CK(cudaMemsetAsync(W.p, 0, n * sizeof(T), st));
     c->launches += 1;
     for (int k = 0; k < nc; ++k) {
@@ -458,7 +461,8 @@ bool same_opts(const dg_mg_opts& a, const dg_mg_opts* b) {
     const dg_mg_opts z{};
     const dg_mg_opts& bb = b ? *b : z;
     return a.coarse == bb.coarse && a.cheb.n_eigs == bb.cheb.n_eigs && a.cheb.n_cheb == bb.cheb.n_cheb &&
-           a.cheb.Lambda == bb.cheb.Lambda && a.cheb.lam_scale == bb.cheb.lam_scale && a.smoother == bb.smoother &&
+           a.cheb.Lambda == bb.cheb.Lambda && a.cheb.lam_scale == bb.cheb.lam_scale &&
+           a.cheb.lam_fixed == bb.cheb.lam_fixed && a.smoother == bb.smoother &&
            a.n_schwarz == bb.n_schwarz && a.local_iters == bb.local_iters && a.local_tol == bb.local_tol &&
            a.schwarz_omega == bb.schwarz_omega;
 }
@@ -660,6 +664,26 @@ int build_hierarchy(const dg_mesh_desc* d, std::vector<LevelHost>& levels, Block
     return DG_OK;
 }
 
+// Boundary tags: values in range, and only Dirichlet on faces that lie on the
+// domain boundary (the faces glued to another block ignore their tag).
+int check_bc(const dg_mesh_desc* d, const BlockTopo& topo, std::string& err) {
+    if (!d->bc) return DG_OK;
+    const int nb = d->n_blocks > 0 ? d->n_blocks : 1;
+    for (int b = 0; b < nb; ++b)
+        for (int f = 0; f < 6; ++f) {
+            const int k = d->bc[6 * b + f];
+            if (k < DG_BC_DIRICHLET || k > DG_BC_ROBIN) {
+                err = "boundary tag out of range";
+                return DG_ERR_INVALID;
+            }
+            if (k != DG_BC_DIRICHLET && topo.face[6 * b + f].nb < 0) {
+                err = "Neumann and Robin boundaries are not implemented (Dirichlet only)";
+                return DG_ERR_UNSUPPORTED;
+            }
+        }
+    return DG_OK;
+}
+
 size_t level_bytes(const LevelHost& h) {
     const size_t nv = h.vqp_off.back(), nd = h.n_dofs(), nm = h.n_mortar_pts;
     size_t b = 0;
@@ -674,21 +698,46 @@ size_t level_bytes(const LevelHost& h) {
 
 }  // namespace
 
+struct dg_mesh {
+    dg_mesh_desc desc{};                // lo, hi, map and warp; array pointers cleared
+    std::vector<dg_block> blocks;
+    std::vector<LevelHost> levels;      // hierarchy, coarsest first
+    BlockTopo topo;
+};
+
 extern "C" {
 
 int dgi_set_error(int code, const char* msg) { return fail(code, msg ? msg : ""); }
 
+int dg_mesh_create(const dg_mesh_desc* d, dg_mesh** out) {
+    if (!out) return fail(DG_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    std::string err;
+    if (!validate_desc(d, err)) return fail(DG_ERR_INVALID, err);
+    auto m = std::make_unique<dg_mesh>();
+    int rc = build_hierarchy(d, m->levels, m->topo, err);
+    if (rc) return fail(rc, err);
+    if ((rc = check_bc(d, m->topo, err))) return fail(rc, err);
+    m->desc = *d;
+    m->desc.leaves = nullptr;
+    m->desc.p = nullptr;
+    m->desc.blocks = nullptr;
+    m->desc.elem_block = nullptr;
+    m->desc.bc = nullptr;
+    if (d->n_blocks > 0) m->blocks.assign(d->blocks, d->blocks + d->n_blocks);
+    *out = m.release();
+    return DG_OK;
+}
+
+void dg_mesh_destroy(dg_mesh* m) { delete m; }
+
 int dg_version(void) { return DGELL_VERSION; }
 const char* dg_last_error(void) { return g_err.c_str(); }
 
-int dg_ctx_footprint(const dg_mesh_desc* mesh, const dg_disc_opts* opts, size_t* bytes) {
+int dg_ctx_footprint(const dg_mesh* mesh, const dg_disc_opts* opts, size_t* bytes) {
     (void)opts;
-    std::string err;
-    if (!validate_desc(mesh, err)) return fail(DG_ERR_INVALID, err);
-    std::vector<LevelHost> lv;
-    BlockTopo topo;
-    int rc = build_hierarchy(mesh, lv, topo, err);
-    if (rc) return fail(rc, err);
+    if (!mesh) return fail(DG_ERR_INVALID, "mesh is NULL");
+    const std::vector<LevelHost>& lv = mesh->levels;
     size_t b = 2 * TabIndex::Count * kTabStride * 12;
     for (auto& h : lv) b += level_bytes(h);
     b += lv.back().n_dofs() * 8 * 6;            // FCG vectors
@@ -697,25 +746,19 @@ int dg_ctx_footprint(const dg_mesh_desc* mesh, const dg_disc_opts* opts, size_t*
 }
 
 
-int dg_ctx_create(const dg_mesh_desc* mesh, const dg_disc_opts* opts, void* stream, dg_ctx** out) {
+int dg_ctx_create(const dg_mesh* mesh, const dg_disc_opts* opts, void* stream, dg_ctx** out) {
     if (!out) return fail(DG_ERR_INVALID, "out is NULL");
     *out = nullptr;
+    if (!mesh) return fail(DG_ERR_INVALID, "mesh is NULL");
     std::string err;
-    if (!validate_desc(mesh, err)) return fail(DG_ERR_INVALID, err);
-    std::vector<LevelHost> lvh;
-    BlockTopo topo;
-    int rc = build_hierarchy(mesh, lvh, topo, err);
-    if (rc) return fail(rc, err);
+    int rc = DG_OK;
+    std::vector<LevelHost> lvh = mesh->levels;
     auto c = std::make_unique<dg_ctx>();
     c->st = (cudaStream_t)stream;
     c->C = (opts && opts->penalty_c > 0) ? opts->penalty_c : 10.0;
-    c->desc = *mesh;
-    c->desc.leaves = nullptr;
-    c->desc.p = nullptr;
-    if (mesh->n_blocks > 0) c->blocks.assign(mesh->blocks, mesh->blocks + mesh->n_blocks);
-    c->desc.blocks = nullptr;
-    c->desc.elem_block = nullptr;
-    c->topo = std::move(topo);
+    c->desc = mesh->desc;
+    c->blocks = mesh->blocks;
+    c->topo = mesh->topo;
     std::vector<double> tab;
     build_tables(tab);
     std::vector<float> tabf(tab.begin(), tab.end());

@@ -128,3 +128,10 @@ struct dg_ctx {
     long long launches = 0;
     dg::ApplyStreams as{};          // side streams of the per-bucket apply
 };
+
+namespace dg {
+// Kernel arguments of level l in precision T: the level's and the context's
+// device pointers (the one definition every apply path uses).
+template <typename T>
+LevelView<T> level_view(dg_ctx* c, int l);
+}  // namespace dg

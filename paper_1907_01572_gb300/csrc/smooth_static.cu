@@ -56,46 +56,6 @@ int scratch_for_current_device(unsigned char** out) {
     return DG_OK;
 }
 
-template <typename T>
-LevelView<T> static_view(dg_ctx* c, int l) {
-    LevelDev& L = c->lv[l];
-    LevelView<T> v{};
-    v.n_elems = L.h.n_elems();
-    v.p = L.p;
-    v.dof_off = L.dof_off;
-    v.vqp_off = L.vqp_off;
-    v.Ob_off = L.Ob_off;
-    v.slot_off = L.slot_off;
-    v.slot_mortar = L.slot_mortar;
-    v.slot_face = L.slot_face;
-    v.slot_side = L.slot_side;
-    v.mortars = L.mortars;
-    if constexpr (sizeof(T) == 8) {
-        v.G = (const T*)L.G64;
-        v.c0 = L.z_active ? (const T*)L.c0_64 : nullptr;
-        v.Ob = L.z_active ? (const T*)L.Ob64 : nullptr;
-        v.mg = (const T*)L.mg64;
-        v.sigma = (const T*)L.sigma64;
-        v.tab = (const T*)c->tab64;
-        v.ftab = (const T*)c->ftab64;
-        v.mt = (T*)L.mt64;
-    } else {
-        v.G = (const T*)L.G32;
-        v.c0 = L.z_active ? (const T*)L.c0_32 : nullptr;
-        v.Ob = L.z_active ? (const T*)L.Ob32 : nullptr;
-        v.mg = (const T*)L.mg32;
-        v.sigma = (const T*)L.sigma32;
-        v.tab = (const T*)c->tab32;
-        v.ftab = (const T*)c->ftab32;
-        v.mt = (T*)L.mt32;
-    }
-    v.ft = c->ft;
-    v.ob_total = (long long)L.ob_count;
-    v.oriented = L.oriented;
-    v.chk = device_check_flag();
-    return v;
-}
-
 #define CKS(call)                                                                          \
     do {                                                                                   \
         cudaError_t _e = (call);                                                           \
@@ -104,7 +64,8 @@ LevelView<T> static_view(dg_ctx* c, int l) {
 
 template <typename T>
 int smooth_static_t(dg_ctx* c, int l, const T* b, T* x, const dg_cheb_opts* o, unsigned char* base) {
-    const int ne = (o && o->n_eigs > 0) ? o->n_eigs : 15;
+    const double fixed = (o && o->lam_fixed > 0) ? o->lam_fixed : 0.0;
+    const int ne = fixed > 0 ? 0 : ((o && o->n_eigs > 0) ? o->n_eigs : 15);
     int nc = (o && o->n_cheb > 0) ? o->n_cheb : 15;
     const double Lam = (o && o->Lambda > 0) ? o->Lambda : 20.0;
     const double scale = (o && o->lam_scale > 0) ? o->lam_scale : 1.0;
@@ -116,9 +77,12 @@ int smooth_static_t(dg_ctx* c, int l, const T* b, T* x, const dg_cheb_opts* o, u
     SmState* sm = reinterpret_cast<SmState*>(base + 3 * kVecBytes);
     Red red{reinterpret_cast<double*>(base + 3 * kVecBytes + kStateBytes), nullptr, nullptr};
     red.out = red.partials + kRedBlocks * 4;
-    red.counter = reinterpret_cast<unsigned*>(red.out + 4);   // zero at load; each last block resets it
+    red.counter = reinterpret_cast<unsigned*>(red.out + 4);   // each last block resets it; cleared below too
     cudaStream_t st = c->st;
-    const LevelView<T> view = static_view<T>(c, l);
+    // The last-block counter must start at zero; a call that stopped early
+    // (an error between launches) may have left it non-zero.
+    CKS(cudaMemsetAsync(red.counter, 0, sizeof(unsigned), st));
+    const LevelView<T> view = level_view<T>(c, l);
     int launches = 0;
     CKS(launch_apply<T>(view, c->lv[l].buckets, x, Ap, st, &launches));
     CKS(residual_init<T>(b, Ap, r, p, n, red, st));
@@ -129,7 +93,7 @@ int smooth_static_t(dg_ctx* c, int l, const T* b, T* x, const dg_cheb_opts* o, u
         CKS(cg_update_fused<T>(sm, x, r, p, Ap, n, red, st));
         CKS(cg_p_update<T>(sm, p, r, n, st));
     }
-    CKS(sm_cheb_coeffs(sm, nc, Lam, scale, st));
+    CKS(sm_cheb_coeffs(sm, nc, Lam, scale, fixed, st));
     CKS(cudaMemsetAsync(p, 0, n * sizeof(T), st));
     for (int k = 0; k < nc; ++k) {
         CKS(launch_apply<T>(view, c->lv[l].buckets, x, Ap, st, &launches));

@@ -17,6 +17,7 @@ DG_OK, DG_ERR_INVALID, DG_ERR_OOM, DG_ERR_CUDA, DG_ERR_NOT_CONVERGED, DG_ERR_BRE
 DG_FP64, DG_FP32, DG_BF16 = 0, 1, 2
 DG_MAP_AFFINE, DG_MAP_SINE_WARP = 0, 1
 DG_BLOCK_HEX8, DG_BLOCK_WEDGE, DG_BLOCK_SHELL = 0, 1, 2
+DG_BC_DIRICHLET, DG_BC_NEUMANN, DG_BC_ROBIN = 0, 1, 2
 
 
 class DgError(RuntimeError):
@@ -35,7 +36,7 @@ class dg_mesh_desc(ctypes.Structure):
                 ("warp_amp", ctypes.c_double), ("warp_k", ctypes.c_int * 3), ("n_elems", ctypes.c_int),
                 ("leaves", ctypes.POINTER(ctypes.c_int)), ("p", ctypes.POINTER(ctypes.c_int)),
                 ("n_blocks", ctypes.c_int), ("blocks", ctypes.POINTER(dg_block)),
-                ("elem_block", ctypes.POINTER(ctypes.c_int))]
+                ("elem_block", ctypes.POINTER(ctypes.c_int)), ("bc", ctypes.POINTER(ctypes.c_int))]
 
 
 class dg_disc_opts(ctypes.Structure):
@@ -50,7 +51,7 @@ class dg_level_info(ctypes.Structure):
 
 class dg_cheb_opts(ctypes.Structure):
     _fields_ = [("n_eigs", ctypes.c_int), ("n_cheb", ctypes.c_int), ("Lambda", ctypes.c_double),
-                ("lam_scale", ctypes.c_double)]
+                ("lam_scale", ctypes.c_double), ("lam_fixed", ctypes.c_double)]
 
 
 class dg_mg_opts(ctypes.Structure):
@@ -86,9 +87,11 @@ _P = ctypes.c_void_p
 _SIGS = {
     "dg_version": ([], ctypes.c_int),
     "dg_last_error": ([], ctypes.c_char_p),
-    "dg_ctx_create": ([ctypes.POINTER(dg_mesh_desc), ctypes.POINTER(dg_disc_opts), _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "dg_mesh_create": ([ctypes.POINTER(dg_mesh_desc), ctypes.POINTER(_P)], ctypes.c_int),
+    "dg_mesh_destroy": ([_P], None),
+    "dg_ctx_create": ([_P, ctypes.POINTER(dg_disc_opts), _P, ctypes.POINTER(_P)], ctypes.c_int),
     "dg_ctx_destroy": ([_P], None),
-    "dg_ctx_footprint": ([ctypes.POINTER(dg_mesh_desc), ctypes.POINTER(dg_disc_opts), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "dg_ctx_footprint": ([_P, ctypes.POINTER(dg_disc_opts), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "dg_level_info_get": ([_P, ctypes.c_int, ctypes.POINTER(dg_level_info)], ctypes.c_int),
     "dg_level_leaves": ([_P, ctypes.c_int, _P, _P, _P], ctypes.c_int),
     "dg_level_blocks": ([_P, ctypes.c_int, _P], ctypes.c_int),
@@ -162,10 +165,15 @@ def _stream():
 
 
 def make_mesh_desc(desc):
-    """dg_mesh_desc from an inputs-style dict (keeps the arrays alive on the struct)."""
+    """dg_mesh_desc from an inputs-style dict (keeps the arrays alive on the struct).
+    An optional "bc" entry gives the dg_bc_kind of each block face (6 per block)."""
     leaves = np.ascontiguousarray(np.asarray(desc["leaves"], dtype=np.int32).reshape(-1, 4))
     p = np.ascontiguousarray(np.asarray(desc["p"], dtype=np.int32).ravel())
     d = dg_mesh_desc()
+    if desc.get("bc") is not None:
+        bc = np.ascontiguousarray(np.asarray(desc["bc"], dtype=np.int32).ravel())
+        d.bc = bc.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        d._keep_bc = bc
     if desc.get("blocks"):
         blocks = (dg_block * len(desc["blocks"]))()
         kinds = {"hex8": DG_BLOCK_HEX8, "wedge": DG_BLOCK_WEDGE, "shell": DG_BLOCK_SHELL}
@@ -279,22 +287,50 @@ def dg_version():
     return lib().dg_version()
 
 
+class Mesh:
+    """Owns a dg_mesh (dg_mesh_create / dg_mesh_destroy) built from an
+    inputs-style description dict."""
+
+    def __init__(self, desc):
+        d = make_mesh_desc(desc)
+        h = ctypes.c_void_p()
+        _check(lib().dg_mesh_create(ctypes.byref(d), ctypes.byref(h)))
+        self.h = h
+
+    def footprint(self, penalty_c=10.0):
+        o = dg_disc_opts(penalty_c)
+        b = ctypes.c_size_t(0)
+        _check(lib().dg_ctx_footprint(self.h, ctypes.byref(o), ctypes.byref(b)))
+        return b.value
+
+    def close(self):
+        if self.h:
+            lib().dg_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def dg_ctx_footprint(desc, penalty_c=10.0):
-    d = make_mesh_desc(desc)
-    o = dg_disc_opts(penalty_c)
-    b = ctypes.c_size_t(0)
-    _check(lib().dg_ctx_footprint(ctypes.byref(d), ctypes.byref(o), ctypes.byref(b)))
-    return b.value
+    m = Mesh(desc)
+    try:
+        return m.footprint(penalty_c)
+    finally:
+        m.close()
 
 
-def cheb_opts(n_eigs=15, n_cheb=15, Lambda=20.0, lam_scale=1.0):
-    return dg_cheb_opts(n_eigs, n_cheb, Lambda, lam_scale)
+def cheb_opts(n_eigs=15, n_cheb=15, Lambda=20.0, lam_scale=1.0, lam_fixed=0.0):
+    return dg_cheb_opts(n_eigs, n_cheb, Lambda, lam_scale, lam_fixed)
 
 
 def mg_opts(n_eigs=15, n_cheb=15, Lambda=20.0, coarse=0, lam_scale=1.0, smoother=0, n_schwarz=3, local_iters=20,
-            local_tol=1e-3, schwarz_omega=0.7):
-    return dg_mg_opts(cheb_opts(n_eigs, n_cheb, Lambda, lam_scale), coarse, smoother, n_schwarz, local_iters,
-                      local_tol, schwarz_omega)
+            local_tol=1e-3, schwarz_omega=0.7, lam_fixed=0.0):
+    return dg_mg_opts(cheb_opts(n_eigs, n_cheb, Lambda, lam_scale, lam_fixed), coarse, smoother, n_schwarz,
+                      local_iters, local_tol, schwarz_omega)
 
 
 def solver_opts(tol=1e-10, max_iter=100, mg_prec=DG_FP64, use_mg=1, graph_mode=0, **mg):
@@ -305,11 +341,16 @@ class Context:
     """Owns a dg_ctx; methods are the C calls of the same name without 'dg_'."""
 
     def __init__(self, desc, penalty_c=10.0, stream=None):
-        d = make_mesh_desc(desc)
+        """desc: an inputs-style description dict or a Mesh."""
+        m = desc if isinstance(desc, Mesh) else Mesh(desc)
         o = dg_disc_opts(penalty_c)
         h = ctypes.c_void_p()
         st = _stream() if stream is None else ctypes.c_void_p(stream)
-        _check(lib().dg_ctx_create(ctypes.byref(d), ctypes.byref(o), st, ctypes.byref(h)))
+        try:
+            _check(lib().dg_ctx_create(m.h, ctypes.byref(o), st, ctypes.byref(h)))
+        finally:
+            if m is not desc:
+                m.close()
         self.h = h
 
     def close(self):
@@ -367,16 +408,16 @@ class Context:
         _check(lib().dg_estimate(self.h, _ptr(u), _ptr(g_qp), _ptr(f_qp), _ptr(gD_qp), _ptr(eta2)))
         return eta2
 
-    def smooth(self, b, x, level=-1, n_eigs=15, n_cheb=15, Lambda=20.0, want_lambda=True):
-        o = cheb_opts(n_eigs, n_cheb, Lambda)
+    def smooth(self, b, x, level=-1, n_eigs=15, n_cheb=15, Lambda=20.0, want_lambda=True, lam_fixed=0.0):
+        o = cheb_opts(n_eigs, n_cheb, Lambda, lam_fixed=lam_fixed)
         lam = ctypes.c_double(0.0)
         _check(lib().dg_smooth(self.h, level, _prec(b), _ptr(b), _ptr(x), ctypes.byref(o),
                                ctypes.byref(lam) if want_lambda else None))
         return lam.value
 
-    def smooth_static(self, b, x, level=-1, n_eigs=15, n_cheb=15, Lambda=20.0, want_lambda=True):
+    def smooth_static(self, b, x, level=-1, n_eigs=15, n_cheb=15, Lambda=20.0, want_lambda=True, lam_fixed=0.0):
         """dg_smooth on the library's fixed scratch array (no device allocation)."""
-        o = cheb_opts(n_eigs, n_cheb, Lambda)
+        o = cheb_opts(n_eigs, n_cheb, Lambda, lam_fixed=lam_fixed)
         lam = ctypes.c_double(0.0)
         _check(lib().dg_smooth_static(self.h, level, _prec(b), _ptr(b), _ptr(x), ctypes.byref(o),
                                       ctypes.byref(lam) if want_lambda else None))

@@ -36,7 +36,8 @@ def test_binding_covers_the_header():
 
 def test_version_and_error_text(lib):
     from paper_1907_01572_gb300 import dgell
-    assert dgell.lib().dg_version() == 115
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "dgell.h")).read()
+    assert dgell.lib().dg_version() == int(re.search(r"#define DGELL_VERSION (\d+)", hdr).group(1))
     assert isinstance(dgell.lib().dg_last_error(), bytes)
 
 
@@ -108,3 +109,51 @@ def test_block_meshes_host_validation(lib):
     kind["blocks"][1]["r1"], kind["blocks"][1]["r2"] = 2.0, 1.0
     with pytest.raises(dgell.DgError):
         dgell.dg_ctx_footprint(kind)
+
+
+def test_mesh_object_and_boundary_tags(lib):
+    """dg_mesh_create / dg_mesh_destroy (no GPU): a mesh object gives the same
+    footprint as the description it was built from; boundary tags are checked
+    -- all Dirichlet accepted, a Neumann or Robin tag on a boundary face
+    rejected as unsupported (this version implements Dirichlet data only), a
+    non-Dirichlet tag on a face glued to another block ignored, a tag out of
+    range rejected as invalid."""
+    import ctypes
+    import numpy as np
+    from paper_1907_01572_gb300 import dgell, inputs
+    d = inputs.config1_mesh()
+    m = dgell.Mesh(d)
+    assert m.footprint() == dgell.dg_ctx_footprint(d)
+    m.close()
+    m.close()    # idempotent on the Python side; dg_mesh_destroy(NULL) is a no-op
+    dgell.lib().dg_mesh_destroy(None)
+    ok = dict(d, bc=np.zeros(6, dtype=np.int32))
+    assert dgell.Mesh(ok).footprint() > 0
+    for kind in (dgell.DG_BC_NEUMANN, dgell.DG_BC_ROBIN):
+        bc = np.zeros(6, dtype=np.int32)
+        bc[3] = kind
+        with pytest.raises(dgell.DgError) as e:
+            dgell.Mesh(dict(d, bc=bc))
+        assert e.value.code == dgell.DG_ERR_UNSUPPORTED
+    with pytest.raises(dgell.DgError) as e:
+        dgell.Mesh(dict(d, bc=np.full(6, 7, dtype=np.int32)))
+    assert e.value.code == dgell.DG_ERR_INVALID
+    # two glued boxes: block 0's face towards block 1 may carry any tag
+    pair = inputs.block_pair_mesh(rot=0, level=1, refine_block=0)
+    probe = dgell.Mesh(pair)
+    probe.close()
+    glued = None
+    for f in range(6):
+        bc = np.zeros(12, dtype=np.int32)
+        bc[f] = dgell.DG_BC_NEUMANN
+        try:
+            dgell.Mesh(dict(pair, bc=bc)).close()
+            glued = f
+        except dgell.DgError as e:
+            assert e.code == dgell.DG_ERR_UNSUPPORTED
+    assert glued is not None
+    # a NULL out pointer and a NULL mesh are invalid arguments
+    desc = dgell.make_mesh_desc(d)
+    assert dgell.lib().dg_mesh_create(ctypes.byref(desc), None) == dgell.DG_ERR_INVALID
+    sz = ctypes.c_size_t(0)
+    assert dgell.lib().dg_ctx_footprint(None, None, ctypes.byref(sz)) == dgell.DG_ERR_INVALID
