@@ -6,6 +6,7 @@ namespace dg {
 
 struct BucketInfo {        // elements of one degree on one level
     const int* elems;      // device element ids
+    const ElemDesc* desc;  // device, per element of the bucket
     int count;
     int max_q;             // largest mortar q among the bucket's slots
     int max_nb;            // largest neighbour n among the bucket's slots

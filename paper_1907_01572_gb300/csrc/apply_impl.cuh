@@ -27,9 +27,16 @@
 // between phases); persistent CTAs stride over the bucket, sized for the most
 // resident warps that shared memory and registers allow; face loops are
 // compiled per mortar size q; FP32 stages every mortar table in shared memory
-// as (Im, Dm) pairs.  An element's mortar records are fetched once (a lane per
-// slot) and its metric terms and per-mortar data are prefetched into L2 while
-// the volume passes run, so the face stages mostly hit L2 instead of DRAM.
+// as (Im, Dm) pairs.  Each element of a bucket has a descriptor (offsets and
+// slot range) and each slot a packed record, so one broadcast load and one
+// load per lane start an element; the next element's descriptor is loaded
+// while the current one runs, and its input and slot records are prefetched
+// into L2.  The element's metric terms and per-mortar data are prefetched into
+// L2 while the volume passes run, so the face stages mostly hit L2 instead of
+// DRAM.  Loops that move global data into shared memory issue all of a lane's
+// loads before its stores.  An element's values sit in shared memory with
+// padded strides (Strides) so that the pencil passes are free of bank
+// conflicts for every N.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -57,6 +64,47 @@ __device__ inline void tangential(int d, int& t1, int& t2) {
 
 // Per-warp arrays start on multiples of four values (16-byte boundaries).
 constexpr int r4(int v) { return (v + 3) & ~3; }
+
+// Shared-memory layout of an element's N^3 values: node (a, b, c) at
+// a + S1 b + S2 c.  The padding puts the 32 lanes of a pencil pass (one
+// x-, y- or z-pencil per lane) into distinct banks where the dense layout
+// does not: N = 8 (rows of 9, planes of 72; dense: 8-way conflicts along x,
+// 4-way along y), N = 4 (planes of 19) and N = 7 (planes of 52).
+template <int N>
+struct Strides {
+    static constexpr int S1 = N == 8 ? 9 : N;
+    static constexpr int S2 = N == 8 ? 72 : (N == 7 ? 52 : N * N);
+    static constexpr int SIZE = S2 * N;
+};
+
+// Padded shared-memory index of the node with element-blocked index k.
+template <int N>
+__device__ __forceinline__ int sidx(int k) {
+    return k % N + Strides<N>::S1 * ((k / N) % N) + Strides<N>::S2 * (k / (N * N));
+}
+
+template <typename T, typename TX>
+__device__ __forceinline__ T ld(const TX* p);
+
+// An element's N^3 input values into shared memory (padded layout).  All of
+// a lane's global loads are issued before its first shared-memory store: the
+// compiler cannot move a load past a store through a generic pointer, so a
+// load-store loop would wait for each load in turn.
+template <int N, typename T, typename TX>
+__device__ __forceinline__ void load_element(const TX* __restrict__ x, T* __restrict__ U, int lane) {
+    constexpr int N3 = N * N * N, R = (N3 + 31) / 32;
+    T v[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const int k = lane + 32 * j;
+        v[j] = k < N3 ? ld<T>(x + k) : T(0);
+    }
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const int k = lane + 32 * j;
+        if (k < N3) U[sidx<N>(k)] = v[j];
+    }
+}
 
 // One (Im, Dm) pair of the mortar tables: a single 8- or 16-byte access.
 template <typename T>
@@ -104,7 +152,8 @@ template <int N, int DIR, bool ACC, int P, typename T>
 __device__ __forceinline__ void pass_rows(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ R,
                                           int t, int nt) {
     constexpr int NP = r4(N);
-    constexpr int stride = DIR == 0 ? 1 : (DIR == 1 ? N : N * N);
+    constexpr int S1 = Strides<N>::S1, S2 = Strides<N>::S2;
+    constexpr int stride = DIR == 0 ? 1 : (DIR == 1 ? S1 : S2);
     T v[P][N];
     int base[P];
     bool ok[P];
@@ -112,7 +161,8 @@ __device__ __forceinline__ void pass_rows(const T* __restrict__ in, T* __restric
     for (int j = 0; j < P; ++j) {
         const int pid = t + j * nt;
         ok[j] = pid < N * N;
-        base[j] = DIR == 0 ? pid * N : (DIR == 1 ? (pid / N) * N * N + (pid % N) : pid);
+        const int u = pid % N, w = pid / N;   // the pencil's two other coordinates
+        base[j] = DIR == 0 ? S1 * u + S2 * w : (DIR == 1 ? u + S2 * w : u + S1 * w);
 #pragma unroll
         for (int m = 0; m < N; ++m) v[j][m] = ok[j] ? in[base[j] + m * stride] : T(0);
     }
@@ -202,7 +252,7 @@ __device__ __forceinline__ void trace_slot(const LevelView<T>& L, const SlotInfo
         return;
     } else {
         constexpr int N2 = N * N, Q2 = Q * Q;
-        const int st[3] = {1, N, N2};
+        const int st[3] = {1, Strides<N>::S1, Strides<N>::S2};
         const int d = s.f >> 1, fn = (s.f & 1) ? N - 1 : 0;
         int t1, t2;
         tangential(d, t1, t2);
@@ -211,6 +261,21 @@ __device__ __forceinline__ void trace_slot(const LevelView<T>& L, const SlotInfo
         T* U1 = df + N2;            // u, d/dt1 u, dn u after the first tangential direction (Q x N)
         T* DU1 = U1 + Q * N;
         T* N1 = DU1 + Q * N;
+        // this side's c at the lane's mortar points, loaded before the face
+        // passes so that the loads overlap them
+        const MortarMap<Q> toA(OR ? s.o : 0);
+        constexpr int R = (Q2 + 31) / 32;
+        T cv[R][3];
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const int k = lane + 32 * j;
+            if (k < Q2) {
+                const int kA = OR ? toA(k % Q, k / Q) : k;
+                cv[j][0] = co[t1 * Q2 + kA];
+                cv[j][1] = co[t2 * Q2 + kA];
+                cv[j][2] = co[d * Q2 + kA];
+            }
+        }
         for (int k = lane; k < N2; k += 32) {
             const int a = k % N, b = k / N;
             const int base = a * st[t1] + b * st[t2];
@@ -244,8 +309,10 @@ __device__ __forceinline__ void trace_slot(const LevelView<T>& L, const SlotInfo
         __syncwarp();
         const T* M2 = sFT + L.ft.off[N - kMinN][Q - kMinN][s.p1];
         T* out = mt + 4 * s.goff + 2 * s.side * Q2;
-        const MortarMap<Q> toA(OR ? s.o : 0);
-        for (int k = lane; k < Q2; k += 32) {
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const int k = lane + 32 * j;
+            if (k >= Q2) continue;
             const int i1 = k % Q, i2 = k / Q, kA = OR ? toA(i1, i2) : k;
             T u = 0, g1 = 0, g2 = 0, gn = 0;
 #pragma unroll
@@ -259,7 +326,66 @@ __device__ __forceinline__ void trace_slot(const LevelView<T>& L, const SlotInfo
                 gn += iv * nb;
             }
             out[kA] = u;
-            out[Q2 + kA] = co[t1 * Q2 + kA] * g1 + co[t2 * Q2 + kA] * g2 + co[d * Q2 + kA] * gn;
+            out[Q2 + kA] = cv[j][0] * g1 + cv[j][1] * g2 + cv[j][2] * gn;
+        }
+        __syncwarp();
+    }
+}
+
+// Lift of one mortar's flux into Y (the transposed mortar interpolation in
+// both tangential directions and the face-normal row of the LGL derivative):
+// PA, PB1, PB2, PBn (Q^2 each, consecutive from PA) are the flux factors at
+// the mortar points; X holds 3 Q N values of scratch.
+template <int N, int Q, typename T>
+__device__ __forceinline__ void lift_apply(const LevelView<T>& L, const SlotInfo<T>& s, T* __restrict__ Y,
+                                           const T* __restrict__ sDL, const T* __restrict__ sFT,
+                                           const T* __restrict__ PA, T* __restrict__ X, int lane) {
+    if constexpr (Q < N) {
+        return;
+    } else {
+        constexpr int N2 = N * N, Q2 = Q * Q;
+        const int st[3] = {1, Strides<N>::S1, Strides<N>::S2};
+        const int d = s.f >> 1, fn = (s.f & 1) ? N - 1 : 0;
+        int t1, t2;
+        tangential(d, t1, t2);
+        const T* PB1 = PA + Q2;
+        const T* PB2 = PB1 + Q2;
+        const T* PBn = PB2 + Q2;
+        T* X1 = X;
+        T* X2 = X1 + Q * N;
+        T* X3 = X2 + Q * N;
+        const T* M2 = sFT + L.ft.off[N - kMinN][Q - kMinN][s.p1];
+        for (int k = lane; k < Q * N; k += 32) {
+            const int i1 = k % Q, b = k / Q;
+            T s1v = 0, s2v = 0, s3v = 0;
+#pragma unroll
+            for (int i2 = 0; i2 < Q; ++i2) {
+                T iv, dv;
+                ld2(M2 + 2 * (i2 * N + b), iv, dv);
+                s1v += iv * PA[i1 + Q * i2] + dv * PB2[i1 + Q * i2];
+                s2v += iv * PB1[i1 + Q * i2];
+                s3v += iv * PBn[i1 + Q * i2];
+            }
+            X1[k] = s1v;
+            X2[k] = s2v;
+            X3[k] = s3v;
+        }
+        __syncwarp();
+        const T* M1 = sFT + L.ft.off[N - kMinN][Q - kMinN][s.p0];
+        for (int k = lane; k < N2; k += 32) {
+            const int a = k % N, b = k / N;
+            T fu = 0, fd = 0;
+#pragma unroll
+            for (int i1 = 0; i1 < Q; ++i1) {
+                T iv, dv;
+                ld2(M1 + 2 * (i1 * N + a), iv, dv);
+                fu += iv * X1[i1 + Q * b] + dv * X2[i1 + Q * b];
+                fd += iv * X3[i1 + Q * b];
+            }
+            const int base = a * st[t1] + b * st[t2];
+            Y[base + fn * st[d]] += fu;
+#pragma unroll
+            for (int c = 0; c < N; ++c) Y[base + c * st[d]] += sDL[fn * N + c] * fd;
         }
         __syncwarp();
     }
@@ -277,7 +403,7 @@ __device__ __forceinline__ void lift_slot(const LevelView<T>& L, const SlotInfo<
         return;
     } else {
         constexpr int N2 = N * N, Q2 = Q * Q;
-        const int st[3] = {1, N, N2};
+        const int st[3] = {1, Strides<N>::S1, Strides<N>::S2};
         const int d = s.f >> 1, fn = (s.f & 1) ? N - 1 : 0;
         int t1, t2;
         tangential(d, t1, t2);
@@ -316,40 +442,7 @@ __device__ __forceinline__ void lift_slot(const LevelView<T>& L, const SlotInfo<
             PBn[k] = b2 * co[d * Q2 + kA];
         }
         __syncwarp();
-        const T* M2 = sFT + L.ft.off[N - kMinN][Q - kMinN][s.p1];
-        for (int k = lane; k < Q * N; k += 32) {
-            const int i1 = k % Q, b = k / Q;
-            T s1v = 0, s2v = 0, s3v = 0;
-#pragma unroll
-            for (int i2 = 0; i2 < Q; ++i2) {
-                T iv, dv;
-                ld2(M2 + 2 * (i2 * N + b), iv, dv);
-                s1v += iv * PA[i1 + Q * i2] + dv * PB2[i1 + Q * i2];
-                s2v += iv * PB1[i1 + Q * i2];
-                s3v += iv * PBn[i1 + Q * i2];
-            }
-            X1[k] = s1v;
-            X2[k] = s2v;
-            X3[k] = s3v;
-        }
-        __syncwarp();
-        const T* M1 = sFT + L.ft.off[N - kMinN][Q - kMinN][s.p0];
-        for (int k = lane; k < N2; k += 32) {
-            const int a = k % N, b = k / N;
-            T fu = 0, fd = 0;
-#pragma unroll
-            for (int i1 = 0; i1 < Q; ++i1) {
-                T iv, dv;
-                ld2(M1 + 2 * (i1 * N + a), iv, dv);
-                fu += iv * X1[i1 + Q * b] + dv * X2[i1 + Q * b];
-                fd += iv * X3[i1 + Q * b];
-            }
-            const int base = a * st[t1] + b * st[t2];
-            Y[base + fn * st[d]] += fu;
-#pragma unroll
-            for (int c = 0; c < N; ++c) Y[base + c * st[d]] += sDL[fn * N + c] * fd;
-        }
-        __syncwarp();
+        lift_apply<N, Q, T>(L, s, Y, sDL, sFT, PA, X1, lane);
     }
 }
 
@@ -368,16 +461,15 @@ __device__ __forceinline__ void lift_slot(const LevelView<T>& L, const SlotInfo<
 // Per-warp shared-memory layout (in values of T) of the warp-per-element kernels.
 template <int N>
 struct Layout {
-    static constexpr int N2 = N * N, N3 = N2 * N, NR = r4(N3);
+    static constexpr int N2 = N * N, N3 = N2 * N, NR = r4(Strides<N>::SIZE);
     static constexpr int TFACE = 2 * N2 + 3 * kQ * N;                 // trace kernel face scratch
     static constexpr int TWARP = NR + TFACE;
+    // Element kernel: Y, A, B, G1, U (the input buffer, dead after the first
+    // volume pass, holds the z-gradient); in the face phase A, B, G1 and U
+    // hold the face scratch (flux factors and lift partial sums).
+    static constexpr bool UALIAS = true;
     static constexpr int EFACE = 4 * kQ * kQ + 3 * kQ * N;            // element kernel face scratch
-    // UALIAS: the input buffer, dead after the first volume pass, holds the
-    // z-gradient, and A, B, G1 (3 arrays) hold the face scratch; else six
-    // arrays with the face scratch in A..G3.
-    static constexpr bool UALIAS = 3 * NR >= EFACE;
-    static constexpr bool ALIAS = UALIAS || 4 * NR >= EFACE;          // face scratch reuses the volume scratch
-    static constexpr int EWARP = UALIAS ? 5 * NR : (ALIAS ? 6 * NR : 6 * NR + EFACE);
+    static constexpr int EWARP = r4(NR + (4 * NR > EFACE ? 4 * NR : EFACE));
 };
 
 // Values ahead of the per-warp scratch: FP32 mortar tables (staged) and the
@@ -443,11 +535,14 @@ template <typename T>
 struct WarpSlots {
     int s0, s1;
     SlotRec<T> mine;
-    __device__ __forceinline__ void load(const LevelView<T>& L, int e, int lane) {
-        s0 = L.slot_off[e];
-        s1 = L.slot_off[e + 1];
+    __device__ __forceinline__ void load(const LevelView<T>& L, int a, int b, int lane) {
+        s0 = a;
+        s1 = b;
         if (s0 + lane < s1) {
-            mine = load_rec(L, s0 + lane);
+            const SlotPack<T> sp = L.spack[s0 + lane];
+            mine.info = sp.info;
+            mine.goff = sp.goff;
+            mine.sig = sp.sig;
         } else {
             mine.info = 0;
             mine.goff = 0;
@@ -509,7 +604,7 @@ __device__ __forceinline__ T* load_tables(const LevelView<T>& L, const T*& sFT, 
 // Warp per element; every element's slot records are fetched once (a lane per
 // slot) instead of through a dependent load chain per slot.
 template <int N, typename T, typename TX, bool OR = true>
-__device__ __forceinline__ void trace_body(const LevelView<T>& L, const int* __restrict__ bucket, int count,
+__device__ __forceinline__ void trace_body(const LevelView<T>& L, const ElemDesc* __restrict__ bdesc, int count,
                                            const TX* __restrict__ x, T* __restrict__ mt, int blk, int nblk) {
     using Ly = Layout<N>;
     constexpr int N3 = Ly::N3;
@@ -519,14 +614,21 @@ __device__ __forceinline__ void trace_body(const LevelView<T>& L, const int* __r
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T* U = wbase + warp * Ly::TWARP;
     T* F = U + Ly::NR;
-    for (int ei = blk * nwarps + warp; ei < count; ei += nblk * nwarps) {
-        const int e = bucket[ei];
-        const long long dofo = L.dof_off[e];
+    const int stride = nblk * nwarps;
+    int ei = blk * nwarps + warp;
+    ElemDesc nd{};
+    if (ei < count) nd = bdesc[ei];
+    for (; ei < count; ei += stride) {
+        const ElemDesc d = nd;
+        const bool more = ei + stride < count;
+        if (more) nd = bdesc[ei + stride];   // the next element's offsets, in flight during this one
+        const long long dofo = d.dofo;
         WarpSlots<T> ws;
-        ws.load(L, e, lane);
-        for (int k = lane; k < N3; k += 32) U[k] = ld<T>(x + dofo + k);
+        ws.load(L, d.s0, d.s1, lane);
+        load_element<N, T, TX>(x + dofo, U, lane);
         __syncwarp();
         ws.prefetch(L, lane, false);   // the mortars' c, into L2 ahead of the later slots
+        if (more) prefetch_l2(x + nd.dofo, N3, lane, 32);   // the next element's input
         for (int si = ws.s0; si < ws.s1; ++si) {
             const SlotInfo<T> s = unpack_rec(ws.get(si));
             const T* co = L.mg + 7 * s.goff + (s.side == 0 ? 1 : 4) * s.q * s.q;
@@ -538,14 +640,48 @@ __device__ __forceinline__ void trace_body(const LevelView<T>& L, const int* __r
 // OR: the level has mortars whose side B face frame is turned (block meshes);
 // without it the mortar-point permutation is compiled out.
 template <int N, typename T, typename TX, bool OR>
-__global__ void trace_kernel(LevelView<T> L, const int* __restrict__ bucket, int count, const TX* __restrict__ x,
+__global__ void trace_kernel(LevelView<T> L, const ElemDesc* __restrict__ bdesc, int count, const TX* __restrict__ x,
                              T* __restrict__ mt) {
-    trace_body<N, T, TX, OR>(L, bucket, count, x, mt, blockIdx.x, gridDim.x);
+    trace_body<N, T, TX, OR>(L, bdesc, count, x, mt, blockIdx.x, gridDim.x);
+}
+
+// f = G g at the volume GL points (G = w det J J^-1 J^-T, six stored values
+// per point, read once: evict-first) and, with a zeroth-order term, B = c0 u.
+// The points of a lane go in batches of up to 8 whose metric loads are all
+// issued before the batch's shared-memory stores (see load_element).
+template <int N, typename T>
+__device__ __forceinline__ void apply_metric(const T* __restrict__ Ge, const T* __restrict__ c0, T* G1, T* G2, T* G3,
+                                             const T* A, T* B, int lane) {
+    constexpr int N3 = N * N * N, R = (N3 + 31) / 32, GB = R < 8 ? R : 8;
+    for (int j0 = 0; j0 < R; j0 += GB) {
+        T m[GB][7];
+#pragma unroll
+        for (int j = 0; j < GB; ++j) {
+            const int k = lane + 32 * (j0 + j);
+            if (j0 + j < R && k < N3) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) m[j][c] = __ldcs(Ge + c * N3 + k);
+                m[j][6] = c0 ? c0[k] : T(0);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < GB; ++j) {
+            const int k = lane + 32 * (j0 + j);
+            if (j0 + j < R && k < N3) {
+                const int s = sidx<N>(k);
+                const T g0 = G1[s], g1 = G2[s], g2 = G3[s];
+                G1[s] = m[j][0] * g0 + m[j][1] * g1 + m[j][2] * g2;
+                G2[s] = m[j][1] * g0 + m[j][3] * g1 + m[j][4] * g2;
+                G3[s] = m[j][2] * g0 + m[j][4] * g1 + m[j][5] * g2;
+                if (c0) B[s] = m[j][6] * A[s];
+            }
+        }
+    }
 }
 
 // BDM: element diagonal blocks only -- 0 never, 1 always, 2 as L.bdiag says.
 template <int N, typename T, typename TX, bool OR = true, int BDM = 2>
-__device__ __forceinline__ void element_body(const LevelView<T>& L, const int* __restrict__ bucket, int count,
+__device__ __forceinline__ void element_body(const LevelView<T>& L, const ElemDesc* __restrict__ bdesc, int count,
                                              const TX* __restrict__ x, T* __restrict__ y, int blk, int nblk) {
     using Ly = Layout<N>;
     constexpr int N3 = Ly::N3, NR = Ly::NR;
@@ -553,21 +689,28 @@ __device__ __forceinline__ void element_body(const LevelView<T>& L, const int* _
     T* wbase = load_tables<N, T>(L, sFT, sI, sDg, sDL);
     const int nwarps = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T* U = wbase + warp * Ly::EWARP;
-    T* Y = U + NR;
+    T* Y = wbase + warp * Ly::EWARP;
     T* A = Y + NR;
     T* B = A + NR;
     T* G1 = B + NR;
-    T* G3 = Ly::UALIAS ? U : G1 + NR;
+    T* U = G1 + NR;
+    T* G3 = U;
     T* G2 = Y;  // the y-gradient lives in Y until the backward passes
-    T* F = Ly::ALIAS ? A : G3 + NR;
+    T* F = A;   // face phase scratch
     const bool mass = L.c0 != nullptr;
-    for (int ei = blk * nwarps + warp; ei < count; ei += nblk * nwarps) {
-        const int e = bucket[ei];
-        const long long dofo = L.dof_off[e], vo = L.vqp_off[e];
+    const int stride = nblk * nwarps;
+    int ei = blk * nwarps + warp;
+    ElemDesc nd{};
+    if (ei < count) nd = bdesc[ei];
+    for (; ei < count; ei += stride) {
+        const ElemDesc d = nd;
+        const bool more = ei + stride < count;
+        if (more) nd = bdesc[ei + stride];   // the next element's offsets, in flight during this one
+        const int e = d.e;
+        const long long dofo = d.dofo, vo = d.vo;
         WarpSlots<T> ws;
-        ws.load(L, e, lane);
-        for (int k = lane; k < N3; k += 32) U[k] = ld<T>(x + dofo + k);
+        ws.load(L, d.s0, d.s1, lane);
+        load_element<N, T, TX>(x + dofo, U, lane);
         prefetch_l2(L.G + 6 * vo, 6 * N3, lane, 32);   // metric terms, needed after 6 passes
         __syncwarp();
         wpass<N, 0, false, false>(U, A, sI, lane);
@@ -576,23 +719,16 @@ __device__ __forceinline__ void element_body(const LevelView<T>& L, const int* _
         __syncwarp();
         wpass<N, 2, false, false>(B, A, sI, lane);  // A = u at GL points
         ws.prefetch(L, lane, true);   // mortar data, needed after the volume terms
+        if (more) {   // the next element's input and slot records
+            prefetch_l2(x + nd.dofo, N3, lane, 32);
+            prefetch_l2(L.spack + nd.s0, nd.s1 - nd.s0, lane, 32);
+        }
         __syncwarp();
         wpass<N, 0, false, false>(A, G1, sDg, lane);
         wpass<N, 1, false, false>(A, G2, sDg, lane);
         wpass<N, 2, false, false>(A, G3, sDg, lane);
         __syncwarp();
-        {
-            const T* Ge = L.G + 6 * vo;
-            for (int k = lane; k < N3; k += 32) {
-                const T g0 = G1[k], g1 = G2[k], g2 = G3[k];
-                const T m00 = Ge[k], m01 = Ge[N3 + k], m02 = Ge[2 * N3 + k];
-                const T m11 = Ge[3 * N3 + k], m12 = Ge[4 * N3 + k], m22 = Ge[5 * N3 + k];
-                G1[k] = m00 * g0 + m01 * g1 + m02 * g2;
-                G2[k] = m01 * g0 + m11 * g1 + m12 * g2;
-                G3[k] = m02 * g0 + m12 * g1 + m22 * g2;
-                if (mass) B[k] = L.c0[vo + k] * A[k];
-            }
-        }
+        apply_metric<N, T>(L.G + 6 * vo, mass ? L.c0 + vo : nullptr, G1, G2, G3, A, B, lane);
         __syncwarp();
         if (mass) wpass<N, 0, true, true>(G1, B, sDg, lane);
         else wpass<N, 0, true, false>(G1, B, sDg, lane);
@@ -614,8 +750,8 @@ __device__ __forceinline__ void element_body(const LevelView<T>& L, const int* _
             for (int k = lane; k < N3; k += 32) {
                 T s = 0;
                 for (int j = 0; j < N3; ++j)   // u from the input vector when its buffer was reused
-                    s += Oe[(long long)j * N3 + k] * (Ly::UALIAS ? ld<T>(x + dofo + j) : U[j]);
-                Y[k] += s;
+                    s += Oe[(long long)j * N3 + k] * (Ly::UALIAS ? ld<T>(x + dofo + j) : U[sidx<N>(j)]);
+                Y[sidx<N>(k)] += s;
             }
             __syncwarp();
         }
@@ -628,7 +764,7 @@ __device__ __forceinline__ void element_body(const LevelView<T>& L, const int* _
             DG_Q_SWITCH(s.q, (lift_slot<N, Q, T, OR, BDM>(L, s, interior, r.sig, Y, sDL, sFT, F, mg, co, L.mt + 4 * s.goff,
                                                  lane)))
         }
-        for (int k = lane; k < N3; k += 32) y[dofo + k] = Y[k];
+        for (int k = lane; k < N3; k += 32) __stcs(y + dofo + k, Y[sidx<N>(k)]);   // written once: evict first
         __syncwarp();
     }
 }
@@ -636,9 +772,9 @@ __device__ __forceinline__ void element_body(const LevelView<T>& L, const int* _
 // BD: the block-diagonal apply of the Schwarz smoother (compiled apart so that
 // the ordinary apply carries no test for it).
 template <int N, typename T, typename TX, bool OR, bool BD = false>
-__global__ void element_kernel(LevelView<T> L, const int* __restrict__ bucket, int count, const TX* __restrict__ x,
+__global__ void element_kernel(LevelView<T> L, const ElemDesc* __restrict__ bdesc, int count, const TX* __restrict__ x,
                                T* __restrict__ y) {
-    element_body<N, T, TX, OR, BD ? 1 : 0>(L, bucket, count, x, y, blockIdx.x, gridDim.x);
+    element_body<N, T, TX, OR, BD ? 1 : 0>(L, bdesc, count, x, y, blockIdx.x, gridDim.x);
 }
 
 // All degree buckets of a level in one launch (used on small levels, where
@@ -648,6 +784,7 @@ struct FusedBuckets {
     int nb;
     int n[kNumN];
     const int* elems[kNumN];
+    const ElemDesc* desc[kNumN];
     int count[kNumN];
     int cta_start[kNumN + 1];
 };
@@ -674,14 +811,14 @@ template <typename T, typename TX>
 __global__ void trace_fused(LevelView<T> L, FusedBuckets fb, const TX* __restrict__ x, T* __restrict__ mt) {
     const int b = fused_bucket(fb);
     const int blk = blockIdx.x - fb.cta_start[b], nblk = fb.cta_start[b + 1] - fb.cta_start[b];
-    DG_BODY_SWITCH(fb.n[b], (trace_body<NN, T, TX>(L, fb.elems[b], fb.count[b], x, mt, blk, nblk)))
+    DG_BODY_SWITCH(fb.n[b], (trace_body<NN, T, TX>(L, fb.desc[b], fb.count[b], x, mt, blk, nblk)))
 }
 
 template <typename T, typename TX>
 __global__ void element_fused(LevelView<T> L, FusedBuckets fb, const TX* __restrict__ x, T* __restrict__ y) {
     const int b = fused_bucket(fb);
     const int blk = blockIdx.x - fb.cta_start[b], nblk = fb.cta_start[b + 1] - fb.cta_start[b];
-    DG_BODY_SWITCH(fb.n[b], (element_body<NN, T, TX>(L, fb.elems[b], fb.count[b], x, y, blk, nblk)))
+    DG_BODY_SWITCH(fb.n[b], (element_body<NN, T, TX>(L, fb.desc[b], fb.count[b], x, y, blk, nblk)))
 }
 
 
@@ -694,7 +831,7 @@ constexpr int kCtaWarps = 8;
 
 template <int N>
 struct CtaLayout {
-    static constexpr int N3 = N * N * N, NR = r4(N3);
+    static constexpr int N3 = N * N * N, NR = r4(Strides<N>::SIZE);
     static constexpr int TWARP = Layout<N>::TFACE;                        // per-warp trace scratch
     static constexpr int TSHARED = NR;                                    // U
     static constexpr int EWARP = NR + 4 * kQ * kQ + 3 * kQ * N;           // per-warp lift accumulator + scratch
@@ -711,7 +848,7 @@ __device__ __forceinline__ void trace_body_cta(const LevelView<T>& L, int e, con
     T* U = base;
     T* F = U + Ly::TSHARED + warp * Ly::TWARP;
     const long long dofo = L.dof_off[e];
-    for (int k = threadIdx.x; k < Ly::N3; k += blockDim.x) U[k] = ld<T>(x + dofo + k);
+    for (int k = threadIdx.x; k < Ly::N3; k += blockDim.x) U[sidx<N>(k)] = ld<T>(x + dofo + k);
     __syncthreads();
     const int s0 = L.slot_off[e], s1 = L.slot_off[e + 1];
     for (int si = s0 + warp; si < s1; si += nw) {
@@ -741,7 +878,7 @@ __device__ __forceinline__ void element_body_cta(const LevelView<T>& L, int e, c
     T* F = Yw + NR;
     const long long dofo = L.dof_off[e], vo = L.vqp_off[e];
     const bool mass = L.c0 != nullptr;
-    for (int k = tid; k < N3; k += nt) U[k] = ld<T>(x + dofo + k);
+    for (int k = tid; k < N3; k += nt) U[sidx<N>(k)] = ld<T>(x + dofo + k);
     __syncthreads();
     wpass<N, 0, false, false>(U, A, sI, tid, nt);
     __syncthreads();
@@ -756,13 +893,14 @@ __device__ __forceinline__ void element_body_cta(const LevelView<T>& L, int e, c
     {
         const T* Ge = L.G + 6 * vo;
         for (int k = tid; k < N3; k += nt) {
-            const T g0 = G1[k], g1 = G2[k], g2 = G3[k];
-            const T m00 = Ge[k], m01 = Ge[N3 + k], m02 = Ge[2 * N3 + k];
-            const T m11 = Ge[3 * N3 + k], m12 = Ge[4 * N3 + k], m22 = Ge[5 * N3 + k];
-            G1[k] = m00 * g0 + m01 * g1 + m02 * g2;
-            G2[k] = m01 * g0 + m11 * g1 + m12 * g2;
-            G3[k] = m02 * g0 + m12 * g1 + m22 * g2;
-            if (mass) B[k] = L.c0[vo + k] * A[k];
+            const int s = sidx<N>(k);
+            const T g0 = G1[s], g1 = G2[s], g2 = G3[s];
+            const T m00 = __ldcs(Ge + k), m01 = __ldcs(Ge + N3 + k), m02 = __ldcs(Ge + 2 * N3 + k);
+            const T m11 = __ldcs(Ge + 3 * N3 + k), m12 = __ldcs(Ge + 4 * N3 + k), m22 = __ldcs(Ge + 5 * N3 + k);
+            G1[s] = m00 * g0 + m01 * g1 + m02 * g2;
+            G2[s] = m01 * g0 + m11 * g1 + m12 * g2;
+            G3[s] = m02 * g0 + m12 * g1 + m22 * g2;
+            if (mass) B[s] = L.c0[vo + k] * A[s];
         }
     }
     __syncthreads();
@@ -785,11 +923,11 @@ __device__ __forceinline__ void element_body_cta(const LevelView<T>& L, int e, c
         const T* Oe = L.Ob + L.Ob_off[e];
         for (int k = tid; k < N3; k += nt) {
             T sacc = 0;
-            for (int j = 0; j < N3; ++j) sacc += Oe[(long long)j * N3 + k] * U[j];
-            Y[k] += sacc;
+            for (int j = 0; j < N3; ++j) sacc += Oe[(long long)j * N3 + k] * U[sidx<N>(j)];
+            Y[sidx<N>(k)] += sacc;
         }
     }
-    for (int k = lane; k < N3; k += 32) Yw[k] = 0;
+    for (int k = lane; k < NR; k += 32) Yw[k] = 0;
     __syncwarp();
     const int s0 = L.slot_off[e], s1 = L.slot_off[e + 1];
     for (int si = s0 + warp; si < s1; si += nw) {
@@ -803,9 +941,10 @@ __device__ __forceinline__ void element_body_cta(const LevelView<T>& L, int e, c
     }
     __syncthreads();
     for (int k = tid; k < N3; k += nt) {
-        T acc = Y[k];
-        for (int w = 0; w < nw; ++w) acc += base[Ly::ESHARED + w * Ly::EWARP + k];
-        y[dofo + k] = acc;
+        const int s = sidx<N>(k);
+        T acc = Y[s];
+        for (int w = 0; w < nw; ++w) acc += base[Ly::ESHARED + w * Ly::EWARP + s];
+        __stcs(y + dofo + k, acc);
     }
 }
 
@@ -882,7 +1021,7 @@ cudaError_t launch_trace(const LevelView<T>& L, const BucketInfo& b, const TX* x
     const size_t smem = shp.smem;
     int grid = (b.count + W - 1) / W;
     if (grid > grid_cap() * per_sm) grid = grid_cap() * per_sm;
-    trace_kernel<N, T, TX, OR><<<grid, W * 32, smem, st>>>(L, b.elems, b.count, x, L.mt);
+    trace_kernel<N, T, TX, OR><<<grid, W * 32, smem, st>>>(L, b.desc, b.count, x, L.mt);
     return cudaGetLastError();
 }
 
@@ -900,7 +1039,7 @@ cudaError_t launch_element(const LevelView<T>& L, const BucketInfo& b, const TX*
     const size_t smem = shp.smem;
     int grid = (b.count + W - 1) / W;
     if (grid > grid_cap() * per_sm) grid = grid_cap() * per_sm;
-    element_kernel<N, T, TX, OR, BD><<<grid, W * 32, smem, st>>>(L, b.elems, b.count, x, y);
+    element_kernel<N, T, TX, OR, BD><<<grid, W * 32, smem, st>>>(L, b.desc, b.count, x, y);
     return cudaGetLastError();
 }
 
@@ -950,6 +1089,7 @@ cudaError_t launch_fused_warp(const LevelView<T>& L, const BucketInfo* buckets, 
         if (b.count == 0) continue;
         fb.n[fb.nb] = n;
         fb.elems[fb.nb] = b.elems;
+        fb.desc[fb.nb] = b.desc;
         fb.count[fb.nb] = b.count;
         fb.cta_start[fb.nb] = ctas;
         ctas += (b.count + W - 1) / W;
@@ -990,6 +1130,7 @@ cudaError_t launch_fused_cta(const LevelView<T>& L, const BucketInfo* buckets, c
         smem_e = std::max(smem_e, (tv + esh + kCtaWarps * ew) * sizeof(T));
         fb.n[fb.nb] = n;
         fb.elems[fb.nb] = b.elems;
+        fb.desc[fb.nb] = b.desc;
         fb.count[fb.nb] = b.count;
         fb.cta_start[fb.nb] = ctas;
         ctas += b.count;

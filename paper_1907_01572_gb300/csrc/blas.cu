@@ -2,6 +2,8 @@
 // Reductions: every block sums a fixed grid-stride slice, reduces it in a fixed
 // tree order and writes one partial; a single block then sums the partials in
 // index order, so repeated runs give bit-identical results.
+#include <algorithm>
+
 #include "blas.h"
 
 namespace dg {
@@ -386,6 +388,23 @@ cudaError_t dots(const T* const* a, const T* const* b, int k, long long n, Red r
 }
 template cudaError_t dots<double>(const double* const*, const double* const*, int, long long, Red, cudaStream_t);
 template cudaError_t dots<float>(const float* const*, const float* const*, int, long long, Red, cudaStream_t);
+
+// Penalty sigma of each slot's mortar into the packed slot records.
+__global__ void slot_sigma_kernel(SlotPack<double>* s64, SlotPack<float>* s32, const int* slot_mortar,
+                                  const double* sigma, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double v = sigma[slot_mortar[i]];
+        s64[i].sig = v;
+        s32[i].sig = (float)v;
+    }
+}
+
+cudaError_t fill_slot_sigma(SlotPack<double>* s64, SlotPack<float>* s32, const int* slot_mortar, const double* sigma,
+                            int n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    slot_sigma_kernel<<<std::min(1024, (n + 255) / 256), 256, 0, st>>>(s64, s32, slot_mortar, sigma, n);
+    return cudaGetLastError();
+}
 
 cudaError_t cast_d2f(const double* s, float* d, long long n, cudaStream_t st) {
     d2f_kernel<<<grid_for(n), 256, 0, st>>>(s, d, n);

@@ -32,6 +32,8 @@ template <typename T>
 cudaError_t dots(const T* const* a, const T* const* b, int k, long long n, Red red, cudaStream_t st);
 
 cudaError_t cast_d2f(const double* s, float* d, long long n, cudaStream_t st);
+cudaError_t fill_slot_sigma(SlotPack<double>* s64, SlotPack<float>* s32, const int* slot_mortar, const double* sigma,
+                            int n, cudaStream_t st);
 cudaError_t cast_f2d(const float* s, double* d, long long n, cudaStream_t st);
 
 // r = b - y; p = r (if p); partial r.r into red (then finalize -> out[0])

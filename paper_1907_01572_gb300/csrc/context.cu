@@ -64,6 +64,7 @@ LevelView<double> level_view<double>(dg_ctx* c, int l) {
     v.slot_face = L.slot_face;
     v.slot_side = L.slot_side;
     v.mortars = L.mortars;
+    v.spack = L.spack64;
     v.mg = L.mg64;
     v.sigma = L.sigma64;
     v.tab = c->tab64;
@@ -93,6 +94,7 @@ LevelView<float> level_view<float>(dg_ctx* c, int l) {
     v.slot_face = L.slot_face;
     v.slot_side = L.slot_side;
     v.mortars = L.mortars;
+    v.spack = L.spack32;
     v.mg = L.mg32;
     v.sigma = L.sigma32;
     v.tab = c->tab32;
@@ -556,6 +558,9 @@ int upload_level(dg_ctx* c, LevelDev& L, int li, std::string& err) {
         BucketInfo& b = L.buckets[n];
         b.count = (int)h.buckets[n].size();
         b.elems = b.count ? A.upload(h.buckets[n], st) : nullptr;
+        std::vector<ElemDesc> ed;
+        for (int e : h.buckets[n]) ed.push_back(ElemDesc{h.dof_off[e], h.vqp_off[e], e, h.slot_off[e], h.slot_off[e + 1], 0});
+        b.desc = b.count ? A.upload(ed, st) : nullptr;
         b.max_q = 2;
         b.max_nb = 2;
         for (int e : h.buckets[n])
@@ -586,6 +591,22 @@ int upload_level(dg_ctx* c, LevelDev& L, int li, std::string& err) {
     L.mt64 = A.alloc<double>(4 * nm);
     L.mt32 = A.alloc<float>(4 * nm);
     L.sigma32 = A.alloc<float>(nmort);
+    {   // slot records (sigma filled in after the mortar geometry)
+        std::vector<SlotPack<double>> sp(h.slot_mortar.size());
+        for (size_t s = 0; s < sp.size(); ++s) {
+            const Mortar& m = h.mortars[h.slot_mortar[s]];
+            const int side = h.slot_side[s];
+            const int p0 = side == 0 ? m.posA0 : m.posB0, p1 = side == 0 ? m.posA1 : m.posB1;
+            sp[s].info = h.slot_face[s] | side << 3 | p0 << 4 | p1 << 6 | (int)m.q << 8 | (m.eB >= 0 ? 1 << 12 : 0) |
+                         (side ? (int)m.orient << 13 : 0);
+            sp[s].sig = 0.0;
+            sp[s].goff = m.goff;
+        }
+        std::vector<SlotPack<float>> sp32(sp.size());
+        for (size_t s = 0; s < sp.size(); ++s) sp32[s] = SlotPack<float>{sp[s].info, 0.f, sp[s].goff};
+        L.spack64 = A.upload(sp, st);
+        L.spack32 = A.upload(sp32, st);
+    }
     int* bad = A.alloc<int>(1);
     double* X = nullptr;
     if (A.failed || cudaMalloc(&X, sizeof(double) * 3 * nd) != cudaSuccess) {
@@ -600,6 +621,7 @@ int upload_level(dg_ctx* c, LevelDev& L, int li, std::string& err) {
     cudaError_t e4 = cast_d2f(L.G64, L.G32, 6 * nv, st);
     cudaError_t e5 = cast_d2f(L.mg64, L.mg32, 7 * nm, st);
     cudaError_t e6 = cast_d2f(L.sigma64, L.sigma32, nmort, st);
+    if (e6 == cudaSuccess) e6 = fill_slot_sigma(L.spack64, L.spack32, L.slot_mortar, L.sigma64, (int)h.slot_mortar.size(), st);
     int hbad = 0;
     cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaError_t e7 = cudaStreamSynchronize(st);

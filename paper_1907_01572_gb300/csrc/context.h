@@ -54,6 +54,8 @@ struct LevelDev {
     Mortar* mortars = nullptr;
     int *slot_off = nullptr, *slot_mortar = nullptr;
     unsigned char *slot_face = nullptr, *slot_side = nullptr;
+    SlotPack<double>* spack64 = nullptr;
+    SlotPack<float>* spack32 = nullptr;
     BucketInfo buckets[kMaxN + 1] = {};
     double *G64 = nullptr, *wdetJ = nullptr, *vxyz = nullptr, *mg64 = nullptr, *sigma64 = nullptr, *bxyz = nullptr;
     float *G32 = nullptr, *mg32 = nullptr, *sigma32 = nullptr;

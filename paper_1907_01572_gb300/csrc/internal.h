@@ -118,6 +118,24 @@ bool build_level_connectivity(LevelHost& L, const BlockTopo& topo, std::string& 
 bool coarsen_level(const LevelHost& fine, LevelHost& coarse, const BlockTopo& topo, std::string& err);
 
 // ---- device level ------------------------------------------------------------------
+// One element of a degree bucket with the offsets its kernels start from
+// (one broadcast load instead of a chain of dependent ones).
+struct ElemDesc {
+    long long dofo, vo;    // DOF and volume GL point offsets
+    int e, s0, s1, pad;    // element id, its mortar slots [s0, s1)
+};
+
+// One mortar slot (an element's side of a mortar), packed for one load:
+// info = face | side << 3 | pos0 << 4 | pos1 << 6 | q << 8 | interior << 12 |
+// orientation of side B's face frame << 13; the mortar's point offset and
+// penalty sigma in the kernel's precision.
+template <typename T>
+struct SlotPack {
+    int info;
+    T sig;
+    long long goff;
+};
+
 template <typename T>
 struct LevelView {         // passed by value to kernels
     int n_elems;
@@ -133,6 +151,7 @@ struct LevelView {         // passed by value to kernels
     const unsigned char* slot_face;
     const unsigned char* slot_side;
     const Mortar* mortars;
+    const SlotPack<T>* spack;   // per slot, in slot order
     const T* mg;           // 7 * n_mortar_pts: [wS, cA0, cA1, cA2, cB0, cB1, cB2] blocks per mortar
     const T* sigma;        // per mortar
     const T* tab;
