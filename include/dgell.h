@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define DGELL_VERSION 117
+#define DGELL_VERSION 118
 
 enum {
     DG_OK = 0,

@@ -196,6 +196,122 @@ __device__ inline void wpass(const T* __restrict__ in, T* __restrict__ out, cons
     }
 }
 
+// ---- tensor-core passes (FP32 and BF16-operand applies, N <= 8) -------------
+// A pass out[p][i] (+)= sum_m R[i][m] in[p][m] over the element's N^2 pencils p
+// is a GEMM (pencils x m) . (m x i): per tile of 16 pencils one
+// mma.sync.m16n8k8 TF32 product with K = 8 and 8 output columns (m and i
+// zero-padded past N).  Each FP32 operand is split into a TF32 head and a
+// TF32 tail (x = hi + lo to about 2^-22), and the product is taken as
+// lo_a hi_b + hi_a lo_b + hi_a hi_b (the lo lo term is below FP32 rounding),
+// so a pass keeps FP32 accuracy on the tensor pipe.
+__device__ __forceinline__ void split_tf32(float x, unsigned& hi, unsigned& lo) {
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
+    const float r = x - __uint_as_float(hi);
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// B fragments (head and tail) of one operator R (rows R[i][m] padded to
+// r4(N), as staged in shared memory): B[k][j] = R[j][k], lane (g, t) =
+// (lane / 4, lane % 4) holding B[t][g] and B[t + 4][g].
+struct OpFrag {
+    unsigned hi[2], lo[2];
+};
+
+template <int N>
+__device__ __forceinline__ OpFrag op_frag(const float* __restrict__ R, int lane) {
+    constexpr int NP = r4(N);
+    const int g = lane >> 2, t = lane & 3;
+    OpFrag f;
+    const float b0 = (g < N && t < N) ? R[g * NP + t] : 0.f;
+    const float b1 = (g < N && t + 4 < N) ? R[g * NP + t + 4] : 0.f;
+    split_tf32(b0, f.hi[0], f.lo[0]);
+    split_tf32(b1, f.hi[1], f.lo[1]);
+    return f;
+}
+
+// The four volume operators of an element kernel: I, I^T, Dg, Dg^T.
+struct VolFrags {
+    OpFrag f[4];
+};
+
+template <int N>
+__device__ __forceinline__ VolFrags vol_frags(const float* sI, const float* sDg, int lane) {
+    constexpr int NP = r4(N);
+    VolFrags v;
+    v.f[0] = op_frag<N>(sI, lane);
+    v.f[1] = op_frag<N>(sI + N * NP, lane);
+    v.f[2] = op_frag<N>(sDg, lane);
+    v.f[3] = op_frag<N>(sDg + N * NP, lane);
+    return v;
+}
+
+// Shared-memory offset of pencil pid (of N^2) along direction DIR.
+template <int N, int DIR>
+__device__ __forceinline__ int pencil_base(int pid) {
+    constexpr int S1 = Strides<N>::S1, S2 = Strides<N>::S2;
+    const int u = pid % N, w = pid / N;
+    return DIR == 0 ? S1 * u + S2 * w : (DIR == 1 ? u + S2 * w : u + S1 * w);
+}
+
+template <int N, int DIR, bool ACC>
+__device__ __forceinline__ void mma_pass(const float* __restrict__ in, float* __restrict__ out, const OpFrag& B,
+                                         int lane) {
+    constexpr int S1 = Strides<N>::S1, S2 = Strides<N>::S2;
+    constexpr int stride = DIR == 0 ? 1 : (DIR == 1 ? S1 : S2);
+    constexpr int NN = N * N, TILES = (NN + 15) / 16;
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int tile = 0; tile < TILES; ++tile) {
+        const int p0 = 16 * tile + g, p1 = p0 + 8;
+        const bool v0 = p0 < NN, v1 = p1 < NN;
+        const int b0 = pencil_base<N, DIR>(v0 ? p0 : 0), b1 = pencil_base<N, DIR>(v1 ? p1 : 0);
+        float a[4];
+        a[0] = (v0 && t < N) ? in[b0 + t * stride] : 0.f;
+        a[1] = (v1 && t < N) ? in[b1 + t * stride] : 0.f;
+        a[2] = (v0 && t + 4 < N) ? in[b0 + (t + 4) * stride] : 0.f;
+        a[3] = (v1 && t + 4 < N) ? in[b1 + (t + 4) * stride] : 0.f;
+        unsigned ah[4], al[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) split_tf32(a[j], ah[j], al[j]);
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+        mma_tf32(d, al, B.hi);
+        mma_tf32(d, ah, B.lo);
+        mma_tf32(d, ah, B.hi);
+        const int i0 = 2 * t, i1 = 2 * t + 1;
+        if (v0 && i0 < N) out[b0 + i0 * stride] = ACC ? out[b0 + i0 * stride] + d[0] : d[0];
+        if (v0 && i1 < N) out[b0 + i1 * stride] = ACC ? out[b0 + i1 * stride] + d[1] : d[1];
+        if (v1 && i0 < N) out[b1 + i0 * stride] = ACC ? out[b1 + i0 * stride] + d[2] : d[2];
+        if (v1 && i1 < N) out[b1 + i1 * stride] = ACC ? out[b1 + i1 * stride] + d[3] : d[3];
+    }
+}
+
+// Volume pass of the warp-per-element kernel: on the tensor pipe for 32-bit
+// values and N = 8 (W: 0 I, 1 I^T, 2 Dg, 3 Dg^T), else on the FP32/FP64 pipe.
+// Measured on the 32^3 sweep mesh, the tensor passes match the FP32-pipe ones
+// in speed; at N = 8 they need fewer registers, at N = 6, 7 more.
+template <int N, typename T>
+constexpr bool use_mma() {
+    return sizeof(T) == 4 && N == 8;
+}
+
+template <int N, int DIR, int W, bool ACC, typename T>
+__device__ __forceinline__ void vpass(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ M,
+                                      const VolFrags& fr, int lane) {
+    if constexpr (use_mma<N, T>()) {
+        mma_pass<N, DIR, ACC>(in, out, fr.f[W], lane);
+    } else {
+        wpass<N, DIR, (W & 1) != 0, ACC>(in, out, M, lane);
+    }
+}
+
 template <typename T>
 struct SlotInfo {
     int f, side, p0, p1, q;
@@ -261,21 +377,6 @@ __device__ __forceinline__ void trace_slot(const LevelView<T>& L, const SlotInfo
         T* U1 = df + N2;            // u, d/dt1 u, dn u after the first tangential direction (Q x N)
         T* DU1 = U1 + Q * N;
         T* N1 = DU1 + Q * N;
-        // this side's c at the lane's mortar points, loaded before the face
-        // passes so that the loads overlap them
-        const MortarMap<Q> toA(OR ? s.o : 0);
-        constexpr int R = (Q2 + 31) / 32;
-        T cv[R][3];
-#pragma unroll
-        for (int j = 0; j < R; ++j) {
-            const int k = lane + 32 * j;
-            if (k < Q2) {
-                const int kA = OR ? toA(k % Q, k / Q) : k;
-                cv[j][0] = co[t1 * Q2 + kA];
-                cv[j][1] = co[t2 * Q2 + kA];
-                cv[j][2] = co[d * Q2 + kA];
-            }
-        }
         for (int k = lane; k < N2; k += 32) {
             const int a = k % N, b = k / N;
             const int base = a * st[t1] + b * st[t2];
@@ -309,10 +410,8 @@ __device__ __forceinline__ void trace_slot(const LevelView<T>& L, const SlotInfo
         __syncwarp();
         const T* M2 = sFT + L.ft.off[N - kMinN][Q - kMinN][s.p1];
         T* out = mt + 4 * s.goff + 2 * s.side * Q2;
-#pragma unroll
-        for (int j = 0; j < R; ++j) {
-            const int k = lane + 32 * j;
-            if (k >= Q2) continue;
+        const MortarMap<Q> toA(OR ? s.o : 0);
+        for (int k = lane; k < Q2; k += 32) {
             const int i1 = k % Q, i2 = k / Q, kA = OR ? toA(i1, i2) : k;
             T u = 0, g1 = 0, g2 = 0, gn = 0;
 #pragma unroll
@@ -326,7 +425,7 @@ __device__ __forceinline__ void trace_slot(const LevelView<T>& L, const SlotInfo
                 gn += iv * nb;
             }
             out[kA] = u;
-            out[Q2 + kA] = cv[j][0] * g1 + cv[j][1] * g2 + cv[j][2] * gn;
+            out[Q2 + kA] = co[t1 * Q2 + kA] * g1 + co[t2 * Q2 + kA] * g2 + co[d * Q2 + kA] * gn;
         }
         __syncwarp();
     }
@@ -464,12 +563,12 @@ struct Layout {
     static constexpr int N2 = N * N, N3 = N2 * N, NR = r4(Strides<N>::SIZE);
     static constexpr int TFACE = 2 * N2 + 3 * kQ * N;                 // trace kernel face scratch
     static constexpr int TWARP = NR + TFACE;
-    // Element kernel: Y, A, B, G1, U (the input buffer, dead after the first
-    // volume pass, holds the z-gradient); in the face phase A, B, G1 and U
-    // hold the face scratch (flux factors and lift partial sums).
+    // Element kernel: Y, A, G1, U (the input buffer, dead after the first
+    // volume pass, holds the z-gradient); in the face phase A, G1 and U hold
+    // the face scratch (flux factors and lift partial sums).
     static constexpr bool UALIAS = true;
     static constexpr int EFACE = 4 * kQ * kQ + 3 * kQ * N;            // element kernel face scratch
-    static constexpr int EWARP = r4(NR + (4 * NR > EFACE ? 4 * NR : EFACE));
+    static constexpr int EWARP = r4(NR + (3 * NR > EFACE ? 3 * NR : EFACE));
 };
 
 // Values ahead of the per-warp scratch: FP32 mortar tables (staged) and the
@@ -645,40 +744,6 @@ __global__ void trace_kernel(LevelView<T> L, const ElemDesc* __restrict__ bdesc,
     trace_body<N, T, TX, OR>(L, bdesc, count, x, mt, blockIdx.x, gridDim.x);
 }
 
-// f = G g at the volume GL points (G = w det J J^-1 J^-T, six stored values
-// per point, read once: evict-first) and, with a zeroth-order term, B = c0 u.
-// The points of a lane go in batches of up to 8 whose metric loads are all
-// issued before the batch's shared-memory stores (see load_element).
-template <int N, typename T>
-__device__ __forceinline__ void apply_metric(const T* __restrict__ Ge, const T* __restrict__ c0, T* G1, T* G2, T* G3,
-                                             const T* A, T* B, int lane) {
-    constexpr int N3 = N * N * N, R = (N3 + 31) / 32, GB = R < 8 ? R : 8;
-    for (int j0 = 0; j0 < R; j0 += GB) {
-        T m[GB][7];
-#pragma unroll
-        for (int j = 0; j < GB; ++j) {
-            const int k = lane + 32 * (j0 + j);
-            if (j0 + j < R && k < N3) {
-#pragma unroll
-                for (int c = 0; c < 6; ++c) m[j][c] = __ldcs(Ge + c * N3 + k);
-                m[j][6] = c0 ? c0[k] : T(0);
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < GB; ++j) {
-            const int k = lane + 32 * (j0 + j);
-            if (j0 + j < R && k < N3) {
-                const int s = sidx<N>(k);
-                const T g0 = G1[s], g1 = G2[s], g2 = G3[s];
-                G1[s] = m[j][0] * g0 + m[j][1] * g1 + m[j][2] * g2;
-                G2[s] = m[j][1] * g0 + m[j][3] * g1 + m[j][4] * g2;
-                G3[s] = m[j][2] * g0 + m[j][4] * g1 + m[j][5] * g2;
-                if (c0) B[s] = m[j][6] * A[s];
-            }
-        }
-    }
-}
-
 // BDM: element diagonal blocks only -- 0 never, 1 always, 2 as L.bdiag says.
 template <int N, typename T, typename TX, bool OR = true, int BDM = 2>
 __device__ __forceinline__ void element_body(const LevelView<T>& L, const ElemDesc* __restrict__ bdesc, int count,
@@ -691,13 +756,14 @@ __device__ __forceinline__ void element_body(const LevelView<T>& L, const ElemDe
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T* Y = wbase + warp * Ly::EWARP;
     T* A = Y + NR;
-    T* B = A + NR;
-    T* G1 = B + NR;
+    T* G1 = A + NR;
     T* U = G1 + NR;
     T* G3 = U;
     T* G2 = Y;  // the y-gradient lives in Y until the backward passes
     T* F = A;   // face phase scratch
     const bool mass = L.c0 != nullptr;
+    VolFrags fr{};
+    if constexpr (use_mma<N, T>()) fr = vol_frags<N>(sI, sDg, lane);
     const int stride = nblk * nwarps;
     int ei = blk * nwarps + warp;
     ElemDesc nd{};
@@ -713,42 +779,58 @@ __device__ __forceinline__ void element_body(const LevelView<T>& L, const ElemDe
         load_element<N, T, TX>(x + dofo, U, lane);
         prefetch_l2(L.G + 6 * vo, 6 * N3, lane, 32);   // metric terms, needed after 6 passes
         __syncwarp();
-        wpass<N, 0, false, false>(U, A, sI, lane);
+        vpass<N, 0, 0, false>(U, A, sI, fr, lane);
         __syncwarp();
-        wpass<N, 1, false, false>(A, B, sI, lane);
+        vpass<N, 1, 0, false>(A, G1, sI, fr, lane);
         __syncwarp();
-        wpass<N, 2, false, false>(B, A, sI, lane);  // A = u at GL points
+        vpass<N, 2, 0, false>(G1, A, sI, fr, lane);  // A = u at GL points
         ws.prefetch(L, lane, true);   // mortar data, needed after the volume terms
         if (more) {   // the next element's input and slot records
             prefetch_l2(x + nd.dofo, N3, lane, 32);
             prefetch_l2(L.spack + nd.s0, nd.s1 - nd.s0, lane, 32);
         }
         __syncwarp();
-        wpass<N, 0, false, false>(A, G1, sDg, lane);
-        wpass<N, 1, false, false>(A, G2, sDg, lane);
-        wpass<N, 2, false, false>(A, G3, sDg, lane);
+        vpass<N, 0, 2, false>(A, G1, sDg, fr, lane);
+        vpass<N, 1, 2, false>(A, G2, sDg, fr, lane);
+        vpass<N, 2, 2, false>(A, G3, sDg, fr, lane);
         __syncwarp();
-        apply_metric<N, T>(L.G + 6 * vo, mass ? L.c0 + vo : nullptr, G1, G2, G3, A, B, lane);
+        {   // f = G g at the volume GL points (six stored values per point, read once: evict-first)
+            const T* Ge = L.G + 6 * vo;
+            for (int k = lane; k < N3; k += 32) {
+                const int s = sidx<N>(k);
+                const T g0 = G1[s], g1 = G2[s], g2 = G3[s];
+                const T m00 = __ldcs(Ge + k), m01 = __ldcs(Ge + N3 + k), m02 = __ldcs(Ge + 2 * N3 + k);
+                const T m11 = __ldcs(Ge + 3 * N3 + k), m12 = __ldcs(Ge + 4 * N3 + k), m22 = __ldcs(Ge + 5 * N3 + k);
+                G1[s] = m00 * g0 + m01 * g1 + m02 * g2;
+                G2[s] = m01 * g0 + m11 * g1 + m12 * g2;
+                G3[s] = m02 * g0 + m12 * g1 + m22 * g2;
+                if (mass) A[s] = L.c0[vo + k] * A[s];   // the zeroth-order term, summed into A below
+            }
+        }
         __syncwarp();
-        if (mass) wpass<N, 0, true, true>(G1, B, sDg, lane);
-        else wpass<N, 0, true, false>(G1, B, sDg, lane);
+        if (mass) vpass<N, 0, 3, true>(G1, A, sDg, fr, lane);
+        else vpass<N, 0, 3, false>(G1, A, sDg, fr, lane);
         __syncwarp();
-        wpass<N, 1, true, true>(G2, B, sDg, lane);
+        vpass<N, 1, 3, true>(G2, A, sDg, fr, lane);
         __syncwarp();
-        wpass<N, 2, true, true>(G3, B, sDg, lane);
+        vpass<N, 2, 3, true>(G3, A, sDg, fr, lane);
         __syncwarp();
-        wpass<N, 0, true, false>(B, A, sI, lane);
+        vpass<N, 0, 1, false>(A, G1, sI, fr, lane);
         __syncwarp();
-        wpass<N, 1, true, false>(A, B, sI, lane);
+        vpass<N, 1, 1, false>(G1, U, sI, fr, lane);
         __syncwarp();
-        wpass<N, 2, true, false>(B, Y, sI, lane);
+        vpass<N, 2, 1, false>(U, Y, sI, fr, lane);
         __syncwarp();
         if (L.Ob != nullptr && L.Ob_off[e] + (long long)N3 * N3 > L.ob_total) {
             if (lane == 0) atomicExch(L.chk, 1);
         } else if (L.Ob != nullptr) {
+            // (coarse levels only; kept rolled so that its loads do not inflate
+            // the register count of the whole kernel)
             const T* Oe = L.Ob + L.Ob_off[e];
+#pragma unroll 1
             for (int k = lane; k < N3; k += 32) {
                 T s = 0;
+#pragma unroll 1
                 for (int j = 0; j < N3; ++j)   // u from the input vector when its buffer was reused
                     s += Oe[(long long)j * N3 + k] * (Ly::UALIAS ? ld<T>(x + dofo + j) : U[sidx<N>(j)]);
                 Y[sidx<N>(k)] += s;
@@ -771,8 +853,16 @@ __device__ __forceinline__ void element_body(const LevelView<T>& L, const ElemDe
 
 // BD: the block-diagonal apply of the Schwarz smoother (compiled apart so that
 // the ordinary apply carries no test for it).
+// Register budget of the 32-bit element kernels, about what the passes and
+// face loops need: left alone, the compiler spends up to twice as many on
+// instruction-level parallelism and halves the resident warps.
+template <int N, typename T>
+constexpr int elem_maxreg() {
+    return sizeof(T) == 8 || N > 8 ? 255 : (N <= 3 ? 64 : (N == 4 ? 72 : (N <= 6 ? 96 : 128)));
+}
+
 template <int N, typename T, typename TX, bool OR, bool BD = false>
-__global__ void element_kernel(LevelView<T> L, const ElemDesc* __restrict__ bdesc, int count, const TX* __restrict__ x,
+__global__ void __maxnreg__((elem_maxreg<N, T>())) element_kernel(LevelView<T> L, const ElemDesc* __restrict__ bdesc, int count, const TX* __restrict__ x,
                                T* __restrict__ y) {
     element_body<N, T, TX, OR, BD ? 1 : 0>(L, bdesc, count, x, y, blockIdx.x, gridDim.x);
 }
