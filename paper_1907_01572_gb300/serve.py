@@ -22,20 +22,53 @@ import numpy as np
 from . import dgell, inputs
 
 
-def make_requests(n=32, rate_hz=20.0, seed=2, full=False):
+# (octree level, degree) of the served Poisson boxes: every uniform box with
+# 1e4 to 5e6 DOFs (13,824 at level 2, p = 5 up to 4,194,304 at level 5, p = 4)
+SERVED_POISSON = [(L, p) for L in range(2, 6) for p in range(3, 9) if 1e4 <= 8 ** L * (p + 1) ** 3 <= 5e6]
+
+
+def make_requests(n=32, rate_hz=20.0, seed=2, full=False, served=False):
     """Seeded mix of Poisson (manufactured sine), star and puncture requests
     with Poisson-process arrival times.  full=False: small meshes (Poisson
     4^3-8^3 elements, p 3..5; star and punctures on box meshes).  full=True:
-    the served workload's sizes -- Poisson 4^3-16^3 elements with p 3..8
-    (4e3 to 3e6 DOFs), the density-jump star and the two punctures on the
-    13-block cubed sphere (shell to r = 20; 1.5e5 to 4.4e5 DOFs)."""
+    Poisson 4^3-16^3 elements with p 3..8 (4e3 to 3e6 DOFs), the density-jump
+    star and the two punctures on the 13-block cubed sphere (shell to r = 20;
+    1.5e5 to 4.4e5 DOFs).  served=True: the served workload -- Poisson boxes
+    drawn uniformly from SERVED_POISSON (1.4e4 to 4.2e6 DOFs), the star and the
+    two punctures on cubed spheres with every block at level 1 or 2 (shell to
+    r = 20; 1.6e4 to 4.4e5 DOFs)."""
     rng = np.random.default_rng(seed)
     t = 0.0
     reqs = []
+    meshes = {}   # one description per mesh key, shared by the requests on that mesh
     for i in range(n):
         t += rng.exponential(1.0 / rate_hz)
         kind = rng.choice(["poisson", "star", "puncture"], p=[0.5, 0.3, 0.2])
-        if kind == "poisson":
+        if kind == "poisson" and served:
+            level, p = SERVED_POISSON[int(rng.integers(len(SERVED_POISSON)))]
+            lv = inputs.uniform_leaves(level)
+            desc = dict(lo=(-1.0, -1.0, -1.0), hi=(1.0, 1.0, 1.0), leaves=np.array(lv, dtype=np.int32),
+                        p=np.full(len(lv), p, dtype=np.int32), warp=None)
+            key = ("poisson", level, p)
+            params = dict(amp=float(rng.uniform(0.5, 2.0)))
+        elif kind == "star" and served:
+            level = int(rng.integers(1, 3))
+            refine = int(rng.integers(0, 2))
+            key = ("star_sphere", level, refine)
+            if key not in meshes:
+                meshes[key] = inputs.star_sphere_mesh(level=level, refine=refine, r_out=20.0)
+            desc = meshes[key]
+            params = dict(amp=float(rng.uniform(0.5, 2.0)))
+        elif kind == "puncture" and served:
+            punc = inputs.two_punctures()
+            level = int(rng.integers(1, 3))
+            key = ("puncture_sphere", level)
+            if key not in meshes:
+                meshes[key] = inputs.puncture_sphere_mesh(punc, level=level)
+            desc = meshes[key]
+            s = float(rng.uniform(0.5, 1.5))
+            params = dict(punctures=[(m, c, tuple(s * np.asarray(P))) for (m, c, P) in punc])
+        elif kind == "poisson":
             level = int(rng.integers(2, 5 if full else 4))
             p = int(rng.integers(3, 9 if full else 6))
             lv = inputs.uniform_leaves(level)
@@ -98,15 +131,17 @@ class Server:
                                          max_iter=300)
             stream.synchronize()
             return u, {"newton_steps": steps, "residual_norm": rn}
-        xyz, bxyz = ctx.quadrature_points()
-        X = xyz.T.cpu().numpy()
+        if not hasattr(ctx, "_qp_host"):   # the mesh's quadrature points, fetched once per context
+            xyz, bxyz = ctx.quadrature_points()
+            ctx._qp_host = (xyz.T.cpu().numpy(), bxyz.T.cpu().numpy())
+        X, XB = ctx._qp_host
         amp = req["params"]["amp"]
         if req["kind"] == "poisson":
             g = amp * 3 * np.pi ** 2 * np.sin(np.pi * X[:, 0]) * np.sin(np.pi * X[:, 1]) * np.sin(np.pi * X[:, 2])
             gd = None
         else:
             g = amp * inputs.star_source(X)
-            gd = torch.tensor(amp * inputs.star_solution(bxyz.T.cpu().numpy()), device="cuda")
+            gd = torch.tensor(amp * inputs.star_solution(XB), device="cuda")
         F = torch.empty(n, dtype=torch.float64, device="cuda")
         ctx.rhs(torch.tensor(g, device="cuda"), gd, F)
         x = torch.zeros_like(F)
