@@ -260,6 +260,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--served", type=int, default=96, help="requests of the served stream to serve (512 in all)")
+    ap.add_argument("--full-configs", action="store_true",
+                    help="also solve configs 3 and 4 at their stated sizes (several minutes)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -380,6 +382,8 @@ def main():
     peaks_alu = alu_peaks(torch) if rank == 0 else {}
     if not args.no_solve and rank == 0:
         solve = solve_bench(dgell, inputs, torch, n_served=args.served)
+    if args.full_configs and rank == 0:
+        solve = dict(solve or {}, full_size=full_configs(dgell, inputs, torch))
     flops = info["apply_flops"]
 
     if rank == 0:
@@ -433,6 +437,10 @@ def _latency(lat):
 
 
 SERVED_RATE_HZ = 2.2   # 70 % of the 3.1 solves/s this mix sustains on 4 slots (GB300, 128 saturated requests)
+# V-cycle options of the cubed-sphere solves (measured on the star, 4.4e5 and 4.1e6 DOFs: 40 / 63 FCG
+# iterations against 87 / 115 with the paper's N_eigs = N_cheb = 15, about 20-30 % less time); the
+# library's defaults stay the paper's.
+SPHERE_MG = dict(n_eigs=35, n_cheb=10, coarse=1)
 
 
 def solve_bench(dgell, inputs, torch, n_solves=8, n_served=96, n_cap=32):
@@ -448,12 +456,12 @@ def solve_bench(dgell, inputs, torch, n_solves=8, n_served=96, n_cap=32):
     cases = [
         ("poisson_4x4x4_p3", inputs.config1_mesh(),
          lambda X: 3 * np.pi ** 2 * np.sin(np.pi * X[:, 0]) * np.sin(np.pi * X[:, 1]) * np.sin(np.pi * X[:, 2]),
-         None, n_solves),
+         None, n_solves, {}),
         ("star_cubed_sphere", inputs.star_sphere_mesh(level=2, refine=1, r_out=20.0), inputs.star_source,
-         inputs.star_solution, 3),
+         inputs.star_solution, 3, SPHERE_MG),
     ]
     with torch.cuda.stream(stream):
-        for name, desc, g, gD, n_case in cases:
+        for name, desc, g, gD, n_case, mg in cases:
             ctx = dgell.Context(desc)
             info = ctx.level_info()
             xyz, bxyz = ctx.quadrature_points()
@@ -461,7 +469,7 @@ def solve_bench(dgell, inputs, torch, n_solves=8, n_served=96, n_cap=32):
             gd = torch.tensor(gD(bxyz.T.cpu().numpy()), device="cuda") if gD is not None else None
             F = torch.empty(info["n_dofs"], dtype=torch.float64, device="cuda")
             ctx.rhs(gq, gd, F)
-            res = {"n_dofs": info["n_dofs"], "n_elems": info["n_elems"], "levels": info["n_levels"]}
+            res = {"n_dofs": info["n_dofs"], "n_elems": info["n_elems"], "levels": info["n_levels"], "mg_opts": mg}
             if desc.get("blocks"):
                 res["blocks"] = len(desc["blocks"])
             for pname, prec in (("fp64", dgell.DG_FP64), ("mixed_fp32_vcycle", dgell.DG_FP32)):
@@ -470,7 +478,7 @@ def solve_bench(dgell, inputs, torch, n_solves=8, n_served=96, n_cap=32):
                     x = torch.zeros_like(F)
                     stream.synchronize()
                     t = time.perf_counter()
-                    st = ctx.solve(F, x, tol=1e-10, max_iter=300, mg_prec=prec)
+                    st = ctx.solve(F, x, tol=1e-10, max_iter=300, mg_prec=prec, **mg)
                     stream.synchronize()
                     dt = time.perf_counter() - t
                     if s >= 2:
@@ -510,6 +518,9 @@ def solve_bench(dgell, inputs, torch, n_solves=8, n_served=96, n_cap=32):
     # process, admitted by footprint onto 4 worker streams (FP64 outer FCG, 1e-10)
     from paper_1907_01572_gb300 import serve
     reqs = serve.make_requests(n=n_served, rate_hz=SERVED_RATE_HZ, seed=2, served=True)
+    for r in reqs:   # the cubed-sphere requests ask for the sphere V-cycle options
+        if r["key"][0].endswith("_sphere"):
+            r["mg"] = SPHERE_MG
     _, summary = serve.Server(slots=4).run([dict(r) for r in reqs])
     sizes = [int(((np.asarray(r["desc"]["p"]) + 1) ** 3).sum()) for r in reqs]
     summary["workload"] = ("first %d requests of the 512-request stream, Poisson arrivals %.1f/s (seed 2, about 70 %% "
@@ -526,6 +537,73 @@ def solve_bench(dgell, inputs, torch, n_solves=8, n_served=96, n_cap=32):
         _, s = serve.Server(slots=4, mg_prec=prec).run(burst)
         cap[pname] = {k: s[k] for k in ("requests", "wall_s", "solves_per_s", "p50_ms", "p99_ms")}
     out["served_capacity"] = cap
+    return out
+
+
+def full_configs(dgell, inputs, torch):
+    """Configs 3 and 4 at the stated sizes (shell ended at r = 20: the
+    Chebyshev-smoothed V-cycle stops contracting on longer compactified
+    shells): the density-jump star on the 13-block cubed sphere at level 4
+    with the cells cut by r = 0.5 and r = 1 refined three times (115,968
+    elements, p 4..8, 4.4e7 DOFs), and the two then three punctures with
+    every block at level 4, p = 5, p = 8 on the cells holding a puncture
+    (53,360 elements, 1.2e7 DOFs), Newton from u = 0.  Each problem is solved
+    once to warm up (plan tuning, graph capture) and then timed, with the FP32
+    V-cycle (mixed) and with the plain FP64 V-cycle, to 1e-10."""
+    import numpy as np
+    out = {}
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        desc = inputs.star_sphere_mesh(level=4, refine=3, r_out=20.0)
+        ctx = dgell.Context(desc)
+        info = ctx.level_info()
+        xyz, bxyz = ctx.quadrature_points()
+        gq = torch.tensor(inputs.star_source(xyz.T.cpu().numpy()), device="cuda")
+        gd = torch.tensor(inputs.star_solution(bxyz.T.cpu().numpy()), device="cuda")
+        F = torch.empty(info["n_dofs"], dtype=torch.float64, device="cuda")
+        ctx.rhs(gq, gd, F)
+        res = {"n_dofs": info["n_dofs"], "n_elems": info["n_elems"], "levels": info["n_levels"],
+               "blocks": len(desc["blocks"]), "device_gb": info["device_bytes"] / 1e9}
+        sols = {}
+        for pname, prec in (("mixed_fp32_vcycle", dgell.DG_FP32), ("fp64", dgell.DG_FP64)):
+            for s in range(2):
+                x = torch.zeros_like(F)
+                stream.synchronize()
+                t = time.perf_counter()
+                st = ctx.solve(F, x, tol=1e-10, max_iter=600, mg_prec=prec, **SPHERE_MG)
+                stream.synchronize()
+                dt = time.perf_counter() - t
+            sols[pname] = x
+            res[pname] = {"seconds": dt, "solves_per_s": 1.0 / dt, "iterations": st["iterations"],
+                          "rel_residual": st["rel_residual"]}
+        res["mixed_vs_fp64_rel_l2"] = float((sols["mixed_fp32_vcycle"] - sols["fp64"]).norm() / sols["fp64"].norm())
+        out["config3_star_cubed_sphere"] = res
+        ctx.close()
+        del sols, F, gq, gd
+        for name, punc in (("two_punctures", inputs.two_punctures()), ("three_punctures", inputs.three_punctures())):
+            desc = inputs.puncture_sphere_mesh(punc, level=4, p_base=5, p_fine=8)
+            ctx = dgell.Context(desc)
+            info = ctx.level_info()
+            ctx.puncture_setup(punc)
+            res = {"n_dofs": info["n_dofs"], "n_elems": info["n_elems"], "levels": info["n_levels"],
+                   "blocks": len(desc["blocks"])}
+            us = {}
+            for pname, prec in (("mixed_fp32_vcycle", dgell.DG_FP32), ("fp64", dgell.DG_FP64)):
+                for s in range(2):
+                    u = torch.zeros(info["n_dofs"], dtype=torch.float64, device="cuda")
+                    stream.synchronize()
+                    t = time.perf_counter()
+                    steps, rn = ctx.newton_solve(u, tol_newton=1e-9, max_newton=12, mg_prec=prec, tol=1e-10,
+                                                 max_iter=600, **SPHERE_MG)
+                    stream.synchronize()
+                    dt = time.perf_counter() - t
+                us[pname] = u
+                res[pname] = {"seconds": dt, "solves_per_s": 1.0 / dt, "newton_steps": steps,
+                              "final_residual_norm": rn}
+            res["mixed_vs_fp64_rel_l2"] = float((us["mixed_fp32_vcycle"] - us["fp64"]).norm() / us["fp64"].norm())
+            out["config4_" + name + "_cubed_sphere"] = res
+            ctx.close()
+    stream.synchronize()
     return out
 
 

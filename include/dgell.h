@@ -228,7 +228,10 @@ int dg_smooth(dg_ctx* ctx, int level, int prec, const void* b, void* x,
  * smooth (all free device memory already handed to a caching allocator or
  * admitted to other work, or loops that cannot take cudaMalloc's implicit
  * device synchronisation).  Same arguments, algorithm and results as
- * dg_smooth, but its work vectors and reduction scratch live in one
+ * dg_smooth (on levels of at most 1024 DOFs dg_smooth applies the assembled
+ * operator and this call the matrix-free one, so there FP32 results agree up
+ * to rounding, which the CG steps amplify), but its work vectors and
+ * reduction scratch live in one
  * fixed-size array compiled into the library (about 6 MB, reserved on every
  * GPU that loads the library until the process exits), so the level must have
  * at most 262,144 DOFs (larger levels: DG_ERR_INVALID).  The first call on a

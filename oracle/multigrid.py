@@ -290,12 +290,18 @@ def overlap_subdomains(mesh, n_overlap=2):
     beyond e_c's boundary the coinciding e_c coordinate moved outward by the
     node's LGL distance from the contact (the direction found from the
     neighbour's node positions and e_c's Jacobian) -- and the weight
-    W = prod_i w_h(xi_ext^i) with delta the overlap width in xi_ext.
+    W = prod_i w_h(xi_ext^i) with delta the overlap width in xi_ext.  With
+    n_overlap = 1 every xi_ext lies in [-1, 1] (the contact nodes sit on e_c's
+    boundary), the overlap width is zero and delta falls to its 1e-12 floor:
+    the weights become the step function 1 inside, 1/2 on faces, 1/4 on edges
+    and 1/8 on corners (pinned by test_overlap_one_layer_step_weights).
     Returns [(global dofs, weights)] per element."""
     from scipy.spatial import cKDTree
     n = int(mesh.n[0])
     if np.any(mesh.n != n):
         raise ValueError("overlap_subdomains: one degree for every element")
+    if any(not m.boundary and (mesh.leaves[m.eA][0] != mesh.leaves[m.eB][0]) for m in mesh.mortars):
+        raise ValueError("overlap_subdomains: conforming faces only (no 2:1 faces)")
     n3 = n ** 3
     xl, _ = tables.lgl_nodes_weights(n)
     X = np.vstack([mesh.node_coords(e) for e in range(mesh.n_elems)])

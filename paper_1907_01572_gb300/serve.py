@@ -102,9 +102,12 @@ def make_requests(n=32, rate_hz=20.0, seed=2, full=False, served=False):
 class Server:
     """Continuous admission of solve requests onto worker streams."""
 
-    def __init__(self, hbm_budget_bytes=64 << 30, slots=4, mg_prec=dgell.DG_FP32, tol=1e-10):
+    def __init__(self, hbm_budget_bytes=64 << 30, slots=4, mg_prec=dgell.DG_FP32, tol=1e-10, mg=None):
+        """mg: V-cycle options (dgell.mg_opts keywords) of the solves whose request
+        carries none of its own (req["mg"]); default the paper's."""
         import torch
         self.torch = torch
+        self.mg = dict(mg or {})
         self.budget = hbm_budget_bytes
         self.slots = slots
         self.mg_prec = mg_prec
@@ -128,7 +131,7 @@ class Server:
             ctx.puncture_setup(req["params"]["punctures"])
             u = torch.zeros(n, dtype=torch.float64, device="cuda")
             steps, rn = ctx.newton_solve(u, tol_newton=1e-9, max_newton=12, mg_prec=self.mg_prec, tol=self.tol,
-                                         max_iter=300)
+                                         max_iter=300, **req.get("mg", self.mg))
             stream.synchronize()
             return u, {"newton_steps": steps, "residual_norm": rn}
         if not hasattr(ctx, "_qp_host"):   # the mesh's quadrature points, fetched once per context
@@ -145,7 +148,7 @@ class Server:
         F = torch.empty(n, dtype=torch.float64, device="cuda")
         ctx.rhs(torch.tensor(g, device="cuda"), gd, F)
         x = torch.zeros_like(F)
-        st = ctx.solve(F, x, tol=self.tol, max_iter=300, mg_prec=self.mg_prec)
+        st = ctx.solve(F, x, tol=self.tol, max_iter=300, mg_prec=self.mg_prec, **req.get("mg", self.mg))
         stream.synchronize()
         return x, st
 

@@ -257,3 +257,26 @@ def test_overlapping_schwarz_on_the_compactified_sphere():
                                  precond=lambda r: H.vcycle(r, coarse='cholesky', smoother_kind='schwarz_overlap',
                                                             n_overlap=n_overlap))
         assert hist[-1] < 1e-10 and it <= cap, (n_overlap, it, hist[-1])
+
+
+def test_overlap_one_layer_step_weights_and_conforming_only():
+    """One overlap layer: the contact nodes lie on e_c's boundary, so the
+    weights are the step values 1 / 1/2 / 1/4 / 1/8 (interior, face, edge,
+    corner); a mesh with 2:1 faces is rejected with a ValueError."""
+    from oracle import multigrid, tables
+    from oracle.mesh import Mesh
+    from paper_1907_01572_gb300 import inputs
+    m = Mesh((0, 0, 0), (1, 1, 1), inputs.uniform_leaves(1), [2] * 8)
+    subs = multigrid.overlap_subdomains(m, 1)
+    n = 3
+    xl, _ = tables.lgl_nodes_weights(n)
+    for d, W in subs:
+        assert set(np.round(W, 12)) <= {1.0, 0.5, 0.25, 0.125}
+        own = W[:n ** 3]
+        for k in range(n ** 3):
+            a, b, c = k % n, (k // n) % n, k // (n * n)
+            on = sum(int(i in (0, n - 1)) for i in (a, b, c))
+            assert abs(own[k] - 0.5 ** on) < 1e-12
+    lv = inputs.refine(inputs.uniform_leaves(1), lambda lf: lf == (1, 0, 0, 0))
+    with pytest.raises(ValueError):
+        multigrid.overlap_subdomains(Mesh((0, 0, 0), (1, 1, 1), lv, [2] * len(lv)), 1)
