@@ -127,9 +127,39 @@ def _jacobian_fn(kind, face):
             x = [R * v[i] / length for i in range(3)]
             params = (r1, r2)
     J = [[sympy.diff(x[i], xi[l]) for l in range(3)] for i in range(3)]
+    H = [[[sympy.diff(x[i], xi[l], xi[m]) for m in range(3)] for l in range(3)] for i in range(3)]
     fn = sympy.lambdify(tuple(xi) + tuple(params), J, "numpy")
+    fh = sympy.lambdify(tuple(xi) + tuple(params), H, "numpy")
     _JAC[key] = fn
+    _HES[key] = fh
     return fn
+
+
+_HES = {}
+
+
+def block_hessian(block, xi):
+    """d^2 x_i / dxi_l dxi_m of the block map at reference points xi (P, 3):
+    (P, 3, 3, 3), from the same symbolic map as block_jacobian."""
+    xi = np.atleast_2d(np.asarray(xi, dtype=np.float64))
+    kind = block["kind"]
+    if kind == "hex8":
+        params = np.asarray(block["corners"], dtype=np.float64).reshape(24)
+        key = ("hex8", None)
+    elif kind == "wedge":
+        params = (float(block["a"]), float(block["r"]))
+        key = ("wedge", int(block["face"]))
+    else:
+        params = (float(block["r1"]), float(block["r2"]))
+        key = ("shell", int(block["face"]))
+    _jacobian_fn(*key)
+    vals = _HES[key](xi[:, 0], xi[:, 1], xi[:, 2], *params)
+    H = np.zeros((len(xi), 3, 3, 3))
+    for i in range(3):
+        for l in range(3):
+            for m in range(3):
+                H[:, i, l, m] = np.broadcast_to(np.asarray(vals[i][l][m], dtype=np.float64), (len(xi),))
+    return H
 
 
 def block_jacobian(block, xi):
@@ -205,6 +235,17 @@ class BlockMesh(Mesh):
         """J[p, i, l] = d x_i / d xi_l of phi_e: the block map's Jacobian times 2^-level."""
         L = int(self.leaves[e][0])
         return block_jacobian(self.blocks[int(self.elem_block[e])], self.block_ref(e, xi)) / (2.0 ** L)
+
+    def hessian_at(self, e, xi):
+        """X[p, i, l, m] = d^2 x_i / dxi_l dxi_m of phi_e: the block map's
+        second derivatives times 4^-level."""
+        L = int(self.leaves[e][0])
+        return block_hessian(self.blocks[int(self.elem_block[e])], self.block_ref(e, xi)) / (4.0 ** L)
+
+    def with_blocks(self, blocks):
+        """The same leaves, degrees and block indices on other block maps (a
+        fiducial grid of identical structure and connectivity)."""
+        return BlockMesh(blocks, self.elem_block, self.leaves, self.p)
 
     def face_point_ref(self, f, b1, b2):
         d, s = divmod(f, 2)

@@ -18,10 +18,18 @@ classofproblems).  Per element e and mortar m:
 
   eta^2(e) = eta^2_e + sum over the mortars touching e of their terms.
 
-Lap u_h is the exact Laplacian of the mapped polynomial u_h(x(xi)) on the
-isoparametric element: with J = dx/dxi, H_xi the reference Hessian of u_h and
-X^k_{lm} = d^2 x_k / dxi_l dxi_m,
-  Hess_x u = J^-T (H_xi - sum_k (du/dx_k) X^k) J^-1,   Lap u = trace.
+Lap u_h is the exact Laplacian of the mapped polynomial u_h(x(xi)): with
+J = dx/dxi, H_xi the reference Hessian of u_h and X^k_{lm} = d^2 x_k / dxi_l dxi_m,
+  Hess_x u = J^-T (H_xi - sum_k (du/dx_k) X^k) J^-1,   Lap u = trace,
+where x(xi) is the element's geometry: the isoparametric interpolant on
+single-box meshes, the exact block map on multi-block meshes (whose J the
+operator uses too; X^k its second derivatives).
+
+Fiducial grid (Sec. II.D, the fiducial-grid paragraph; Problem C's
+compactified grid): with `fiducial`, a mesh of identical structure and
+connectivity on other block maps, the integrands R_e, J_{m,.} stay those of
+the physical grid while the integration weights (w det J, w S^m) and h_e, h_m
+and sigma come from the fiducial grid.
 Every quantity is evaluated at the element's GL points (p + 1 per direction)
 and the mortar's GL points (p_m + 1 per direction), the quadrature of the
 operator itself.
@@ -47,7 +55,11 @@ Readings (where the paper leaves the choice open or prints something odd):
 Pins: closed forms for a constant source, an element indicator function
 (conforming and 2:1 mortars) and a kink across a plane; zero for a quadratic
 solution on affine elements and for a linear solution on curved ones
-(tests/test_oracle_estimator.py).
+(tests/test_oracle_estimator.py); on block meshes the map's second
+derivatives against differences of its Jacobian, Lap u_h of the interpolant
+of a smooth field against that field's Laplacian on curved wedge and shell
+elements, and the exact scaling of the three estimator terms (s^5, s^3, s^0)
+under a uniformly scaled fiducial grid (tests/test_oracle_estimator_blocks.py).
 """
 import numpy as np
 
@@ -117,8 +129,11 @@ def laplacian_at_gl(mesh, e, ue):
     xi, w, J, detJ, Jinv = volume_geometry(mesh, e)
     Psi, dPsi = tables.basis3d(xl, xi)
     d2Psi = basis3d_second(xl, xi)
-    X = mesh.node_coords(e)
-    Xss = np.einsum('lmpa,ai->pilm', d2Psi, X)          # d^2 x_i / dxi_l dxi_m
+    if hasattr(mesh, "hessian_at"):                     # exact block map
+        Xss = mesh.hessian_at(e, xi)
+    else:                                               # isoparametric interpolant
+        X = mesh.node_coords(e)
+        Xss = np.einsum('lmpa,ai->pilm', d2Psi, X)      # d^2 x_i / dxi_l dxi_m
     u = Psi @ ue
     du = np.einsum('lpa,a->pl', dPsi, ue)               # du / dxi_l
     d2u = np.einsum('lmpa,a->plm', d2Psi, ue)           # d^2 u / dxi_l dxi_m
@@ -129,7 +144,7 @@ def laplacian_at_gl(mesh, e, ue):
     return lap, u, w * detJ
 
 
-def _volume_term(mesh, e, u, g_fn, f_fn):
+def _volume_term(mesh, e, u, g_fn, f_fn, fid=None):
     from .sipg import volume_points
     ue = u[mesh.dof_off[e]:mesh.dof_off[e + 1]]
     lap, uq, wd = laplacian_at_gl(mesh, e, ue)
@@ -137,51 +152,67 @@ def _volume_term(mesh, e, u, g_fn, f_fn):
     g = g_fn(xq) if g_fn is not None else 0.0
     f = f_fn(xq) if f_fn is not None else 0.0
     R = f * uq - g - lap
-    he = element_diameter(mesh, e)
+    if fid is not None:                                 # weights and h_e of the fiducial grid
+        xi, w, J, detJ, Jinv = volume_geometry(fid, e)
+        wd = w * detJ
+    he = element_diameter(mesh if fid is None else fid, e)
     pe = float(mesh.p[e])
     return he * he * pe * pe * float(np.sum(wd * R * R))
 
 
-def _mortar_term(mesh, mi, u, gD_fn, C):
+def _mortar_term(mesh, mi, u, gD_fn, C, fid=None):
     """eta^2_{m,1} + eta^2_{m,2} (interior) or eta^2_{m,3} (Dirichlet) of mortar mi."""
+    return sum(_mortar_terms(mesh, mi, u, gD_fn, C, fid))
+
+
+def _mortar_terms(mesh, mi, u, gD_fn, C, fid=None):
+    """(eta^2_{m,1}, eta^2_{m,2} or eta^2_{m,3}) of mortar mi."""
     m = mesh.mortars[mi]
     md = MortarData(mesh, mi, C)
-    hm = min(h.min() for h in md.h)
+    mw = md if fid is None else MortarData(fid, mi, C)   # weights, h_m and sigma
+    hm = min(h.min() for h in mw.h)
     pm = float(m.pm)
     uA = u[mesh.dof_off[m.eA]:mesh.dof_off[m.eA + 1]]
     vA = md.psi[0] @ uA
     if m.eB is None:
         gD = gD_fn(md.x) if gD_fn is not None else 0.0
         J3 = vA - gD
-        return md.sigma / hm * pm * pm * float(np.sum(md.W * J3 * J3))
+        return 0.0, mw.sigma / hm * pm * pm * float(np.sum(mw.W * J3 * J3))
     uB = u[mesh.dof_off[m.eB]:mesh.dof_off[m.eB + 1]]
     J1 = md.dn[0] @ uA - md.dn[1] @ uB
     J2 = vA - md.psi[1] @ uB
-    return hm / pm * float(np.sum(md.W * J1 * J1)) + md.sigma / hm * pm * pm * float(np.sum(md.W * J2 * J2))
+    return hm / pm * float(np.sum(mw.W * J1 * J1)), mw.sigma / hm * pm * pm * float(np.sum(mw.W * J2 * J2))
 
 
-def estimate(mesh, u, g_fn=None, f_fn=None, gD_fn=None, C=10.0, parts=False, elems=None):
-    """eta^2(e) for every element of `mesh` (oracle Mesh, single box), or for
+def estimate(mesh, u, g_fn=None, f_fn=None, gD_fn=None, C=10.0, parts=False, elems=None, fiducial=None):
+    """eta^2(e) for every element of `mesh` (oracle Mesh or BlockMesh), or for
     the elements listed in `elems` only (in that order).
 
     u: nodal coefficients (n_dofs,); g_fn, f_fn, gD_fn: callables of physical
-    points (P, 3) -> (P,) or None for zero.  With parts=True also returns the
-    volume part and the mortar part separately.
+    points (P, 3) -> (P,) or None for zero.  fiducial: a BlockMesh of identical
+    structure (mesh.with_blocks(...)) whose geometry supplies the weights,
+    h_e, h_m and sigma, or None.  With parts=True also returns the volume part
+    and the mortar part separately.
     """
     u = np.asarray(u, dtype=np.float64)
+    fid = fiducial
+    if fid is not None:
+        same = all((a.eA, a.fA, a.eB, a.fB) == (b.eA, b.fA, b.eB, b.fB) for a, b in zip(mesh.mortars, fid.mortars))
+        if fid.n_elems != mesh.n_elems or len(fid.mortars) != len(mesh.mortars) or not same:
+            raise ValueError("estimate: the fiducial grid must have the mesh's structure and connectivity")
     sel = list(range(mesh.n_elems)) if elems is None else [int(e) for e in elems]
     pos = {e: i for i, e in enumerate(sel)}
     vol = np.zeros(len(sel))
     mort = np.zeros(len(sel))
     for i, e in enumerate(sel):
-        vol[i] = _volume_term(mesh, e, u, g_fn, f_fn)
+        vol[i] = _volume_term(mesh, e, u, g_fn, f_fn, fid)
     if elems is None:
         mortars = range(len(mesh.mortars))
     else:
         mortars = sorted({mi for e in sel for f in range(6) for mi in mesh.elem_mortars[e][f]})
     for mi in mortars:
         m = mesh.mortars[mi]
-        t = _mortar_term(mesh, mi, u, gD_fn, C)
+        t = _mortar_term(mesh, mi, u, gD_fn, C, fid)
         for e in (m.eA, m.eB):
             if e is not None and e in pos:
                 mort[pos[e]] += t

@@ -158,6 +158,19 @@ def star_source(x):
     return 4 * np.pi * star_density(np.linalg.norm(x, axis=1))
 
 
+# ---- Lorentzian (Problem C): u = (1 + r^2)^(-1/2), solving -Lap u = 3 (1 + r^2)^(-5/2) ----
+def lorentzian_solution(x):
+    x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
+    return 1.0 / np.sqrt(1.0 + np.sum(x * x, axis=1))
+
+
+def lorentzian_source(x):
+    """g of -Lap u = g for the Lorentzian (the coercive sign; the printed
+    equation carries the opposite sign, which the closed form does not satisfy)."""
+    x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
+    return 3.0 * (1.0 + np.sum(x * x, axis=1)) ** -2.5
+
+
 def _cell_bounds(lf, lo, hi):
     L, i, j, k = lf
     w = (np.asarray(hi) - np.asarray(lo)) / (1 << L)

@@ -83,3 +83,23 @@ def test_jacobian_matches_finite_differences():
     eps = 1e-6
     fd = (prob.residual(u + eps * v) - prob.residual(u - eps * v)) / (2 * eps)
     assert np.linalg.norm(Jv - fd) < 1e-6 * np.linalg.norm(fd)
+
+
+def test_lorentzian_closed_form_and_sign():
+    """Problem C's Lorentzian u = (1 + r^2)^(-1/2): -Lap u equals the source
+    3 (1 + r^2)^(-5/2) (central differences in all three directions at random
+    points), so the printed +3 on the Laplacian side is a sign slip (reading
+    A2: the coercive form -Lap u = g is solved)."""
+    rng = np.random.default_rng(3)
+    X = rng.uniform(-3, 3, (20, 3))
+    h = 1e-3
+    u = inputs.lorentzian_solution
+    lap = -6 * u(X)
+    for d in range(3):
+        e = np.zeros(3)
+        e[d] = h
+        lap = lap + u(X + e) + u(X - e)
+    lap /= h * h
+    g = inputs.lorentzian_source(X)
+    assert np.abs(-lap - g).max() < 1e-5 * np.abs(g).max()
+    assert np.abs(lap - g).max() > 0.5 * np.abs(g).max()      # the printed sign does not hold
