@@ -437,8 +437,11 @@ def _latency(lat):
 
 
 SERVED_RATE_HZ = 2.2   # 70 % of the 3.1 solves/s this mix sustains on 4 slots (GB300, 128 saturated requests)
-# V-cycle options of the cubed-sphere solves (measured on the star, 4.4e5 and 4.1e6 DOFs: 40 / 63 FCG
-# iterations against 87 / 115 with the paper's N_eigs = N_cheb = 15, about 20-30 % less time); the
+# V-cycle options of the star solves on the cubed sphere (measured at 4.4e5 and 4.1e6 DOFs: 40 / 63 FCG
+# iterations against 87 / 115 with the paper's N_eigs = N_cheb = 15, about 20-30 % less time).  The
+# Newton problems and the served mix keep the paper's options: the exact coarse solve's setup (the
+# level-0 operator assembled by applies and inverted on the host, per context and, for Newton, per
+# Jacobian) cost the served mix far more than it saved (capacity 0.46 against 3.0 solves/s).  The
 # library's defaults stay the paper's.
 SPHERE_MG = dict(n_eigs=35, n_cheb=10, coarse=1)
 
@@ -518,9 +521,6 @@ def solve_bench(dgell, inputs, torch, n_solves=8, n_served=96, n_cap=32):
     # process, admitted by footprint onto 4 worker streams (FP64 outer FCG, 1e-10)
     from paper_1907_01572_gb300 import serve
     reqs = serve.make_requests(n=n_served, rate_hz=SERVED_RATE_HZ, seed=2, served=True)
-    for r in reqs:   # the cubed-sphere requests ask for the sphere V-cycle options
-        if r["key"][0].endswith("_sphere"):
-            r["mg"] = SPHERE_MG
     _, summary = serve.Server(slots=4).run([dict(r) for r in reqs])
     sizes = [int(((np.asarray(r["desc"]["p"]) + 1) ** 3).sum()) for r in reqs]
     summary["workload"] = ("first %d requests of the 512-request stream, Poisson arrivals %.1f/s (seed 2, about 70 %% "
@@ -594,7 +594,7 @@ def full_configs(dgell, inputs, torch):
                     stream.synchronize()
                     t = time.perf_counter()
                     steps, rn = ctx.newton_solve(u, tol_newton=1e-9, max_newton=12, mg_prec=prec, tol=1e-10,
-                                                 max_iter=600, **SPHERE_MG)
+                                                 max_iter=600)
                     stream.synchronize()
                     dt = time.perf_counter() - t
                 us[pname] = u

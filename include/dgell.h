@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define DGELL_VERSION 118
+#define DGELL_VERSION 120
 
 enum {
     DG_OK = 0,
@@ -361,18 +361,34 @@ int dg_transfer(dg_ctx* ctx, int coarse_level, int prec, int direction, const vo
  * those of the operator's penalty (eq. penaltyparameter), Lap u the exact
  * Laplacian of the mapped polynomial on the isoparametric element, and
  * every norm by the operator's own GL quadrature.  Each interior mortar's
- * terms count in full for both of its elements.
+ * terms count in full for both of its elements.  Geometry: the isoparametric
+ * interpolant on single-box meshes, the exact block maps (with their second
+ * derivatives in Lap u) on multi-block meshes, as in the operator.
  * u: device double, n_dofs; g_qp, f_qp: device double values at the finest
  * level's volume GL points (dg_quadrature_points order), NULL for 0 (pass
  * the coefficient given to dg_set_zeroth_order as f_qp); gD_qp: device
  * double values at the Dirichlet mortar points, NULL for 0.  eta2: device
- * double, n_elems (output).  Single-box meshes only (DG_ERR_UNSUPPORTED with
- * blocks).  Queues one FP64 apply of u (overwriting the level's trace
- * buffer), a node-coordinate kernel and the estimator kernel; takes
- * 4 n_dofs doubles of stream-ordered scratch (cudaMallocAsync) for the
- * duration of the call.  Asynchronous. */
+ * double, n_elems (output).  Queues one FP64 apply of u (overwriting the
+ * level's trace buffer), on single boxes a node-coordinate kernel, and the
+ * estimator kernel; takes n_dofs doubles (single box: 4 n_dofs) of
+ * stream-ordered scratch (cudaMallocAsync) for the duration of the call.
+ * Asynchronous. */
 int dg_estimate(dg_ctx* ctx, const double* u, const double* g_qp, const double* f_qp, const double* gD_qp,
                 double* eta2);
+
+/* dg_estimate with a fiducial grid (Sec. II.D, the fiducial-grid paragraph;
+ * Problem C's compactified grid): on a multi-block mesh, `fiducial` (HOST,
+ * n_fiducial = the mesh's block count) gives other maps for the same blocks
+ * (same kinds and cube faces, other corners or radii; e.g. the shell pulled
+ * in from r2 = 1e9 to a moderate radius).  The integrands R_e and J_{m,.}
+ * stay those of the physical grid; the weights of every norm (w det J,
+ * w S^m), h_e, h_m and sigma are the fiducial grid's.  fiducial = NULL is
+ * dg_estimate.  The geometry of the mortars on the fiducial grid is computed
+ * into stream-ordered scratch (7 doubles per mortar point) for the call.
+ * DG_ERR_INVALID: single-box mesh with a fiducial grid, block count, kinds or
+ * faces that differ, or a fiducial grid that folds a face. */
+int dg_estimate_fiducial(dg_ctx* ctx, const dg_block* fiducial, int n_fiducial, const double* u,
+                         const double* g_qp, const double* f_qp, const double* gD_qp, double* eta2);
 
 /* hp-AMR driving strategy (Sec. II.D, Algorithm 4, smooth-pred).  Host code,
  * no context and no GPU needed. */

@@ -109,6 +109,81 @@ __host__ __device__ inline void block_jacobian(const dg_block& B, const double x
     }
 }
 
+// H[i][l][m] = d^2 x_i / dxi_l dxi_m of the block map at xi (the second
+// derivatives of the formulas in block_point, for the estimator's exact
+// Laplacian of mapped polynomials).  Wedge and shell, with v linear in
+// xi_0, xi_1, u = v / |v|, t = (xi_2 + 1) / 2 and a, b in {0, 1} along e_ta:
+//   d_a u_i = (delta_i,ta - u_i u_ta) / |v|,
+//   d_a d_b u_i = -[(d_b u_i) u_ta + u_i (d_b u_ta) + (d_a u_i) u_tb] / |v|;
+//   wedge x = (1 - t) a v + t r u: d_a d_b x = t r d_a d_b u,
+//     d_a d_2 x = (r d_a u - a e_ta) / 2, d_2 d_2 x = 0;
+//   shell x = R(t) u: d_a d_b x = R d_a d_b u, d_a d_2 x = R' d_a u / 2,
+//     d_2 d_2 x = R'' u / 4, R' = R^2 (1/r1 - 1/r2), R'' = 2 R R' (1/r1 - 1/r2).
+__host__ __device__ inline void block_hessian(const dg_block& B, const double xi[3], double H[3][3][3]) {
+    for (int i = 0; i < 3; ++i)
+        for (int l = 0; l < 3; ++l)
+            for (int m = 0; m < 3; ++m) H[i][l][m] = 0.0;
+    if (B.kind == DG_BLOCK_HEX8) {
+        for (int c = 0; c < 8; ++c) {
+            double f[3], df[3];
+            for (int k = 0; k < 3; ++k) {
+                const bool hi = (c >> k) & 1;
+                f[k] = hi ? 0.5 * (1.0 + xi[k]) : 0.5 * (1.0 - xi[k]);
+                df[k] = hi ? 0.5 : -0.5;
+            }
+            const double w01 = df[0] * df[1] * f[2], w02 = df[0] * f[1] * df[2], w12 = f[0] * df[1] * df[2];
+            for (int i = 0; i < 3; ++i) {
+                H[i][0][1] += w01 * B.corners[c][i];
+                H[i][0][2] += w02 * B.corners[c][i];
+                H[i][1][2] += w12 * B.corners[c][i];
+            }
+        }
+        for (int i = 0; i < 3; ++i) {
+            H[i][1][0] = H[i][0][1];
+            H[i][2][0] = H[i][0][2];
+            H[i][2][1] = H[i][1][2];
+        }
+        return;
+    }
+    int d, t1, t2;
+    double sg;
+    wedge_frame(B.face, d, sg, t1, t2);
+    double v[3];
+    v[d] = sg;
+    v[t1] = xi[0];
+    v[t2] = xi[1];
+    const double len = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    const int ta[2] = {t1, t2};
+    double u[3], du[2][3], ddu[2][2][3];
+    for (int i = 0; i < 3; ++i) u[i] = v[i] / len;
+    for (int a = 0; a < 2; ++a)
+        for (int i = 0; i < 3; ++i) du[a][i] = ((i == ta[a] ? 1.0 : 0.0) - u[i] * u[ta[a]]) / len;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int i = 0; i < 3; ++i)
+                ddu[a][b][i] = -(du[b][i] * u[ta[a]] + u[i] * du[b][ta[a]] + du[a][i] * u[ta[b]]) / len;
+    const double t = 0.5 * (xi[2] + 1.0);
+    if (B.kind == DG_BLOCK_WEDGE) {
+        for (int i = 0; i < 3; ++i) {
+            for (int a = 0; a < 2; ++a) {
+                for (int b = 0; b < 2; ++b) H[i][a][b] = t * B.r * ddu[a][b][i];
+                H[i][a][2] = H[i][2][a] = 0.5 * (B.r * du[a][i] - B.a * (i == ta[a] ? 1.0 : 0.0));
+            }
+        }
+    } else {
+        const double k = 1.0 / B.r1 - 1.0 / B.r2;
+        const double R = 1.0 / ((1.0 - t) / B.r1 + t / B.r2);
+        const double dR = R * R * k, ddR = 2.0 * R * dR * k;
+        for (int i = 0; i < 3; ++i) {
+            for (int a = 0; a < 2; ++a) {
+                for (int b = 0; b < 2; ++b) H[i][a][b] = R * ddu[a][b][i];
+                H[i][a][2] = H[i][2][a] = 0.5 * dR * du[a][i];
+            }
+            H[i][2][2] = 0.25 * ddR * u[i];
+        }
+    }
+}
+
 // Relative orientation of two faces, o = swap | flip1 << 1 | flip2 << 2:
 // side A's face coordinates (u, v) (along its tangential axes in increasing
 // order) become side B's as (w1, w2) = swap ? (v, u) : (u, v), then w1 and w2

@@ -358,8 +358,11 @@ TransferView<T> tview(dg_ctx* c, int lc) {
 
 // coarse-grid solve support: dense inverse of the level-0 operator (FP64),
 // assembled column by column with the matrix-free apply.
+// Dense inverse of the level-0 operator for the exact coarse solve, rebuilt
+// whenever the operator's coefficients change (a new zeroth-order term, e.g.
+// every Newton step).
 int ensure_coarse_inverse(dg_ctx* c) {
-    if (c->coarse_ready) return DG_OK;
+    if (c->coarse_ready && c->coarse_version == c->op_version) return DG_OK;
     const int n = (int)c->lv[0].h.n_dofs();
     if (n > 4096) return fail(DG_ERR_UNSUPPORTED, "coarse Cholesky needs level 0 with at most 4096 dofs");
     double* E = nullptr;
@@ -407,12 +410,13 @@ int ensure_coarse_inverse(dg_ctx* c) {
             inv[(size_t)col * n + i] = t / Lc[(size_t)i * n + i];
         }
     }
-    c->coarse_inv = c->arena.alloc<double>((size_t)n * n);
+    if (!c->coarse_inv) c->coarse_inv = c->arena.alloc<double>((size_t)n * n);   // level 0's size never changes
     if (!c->coarse_inv) return fail(DG_ERR_OOM, "device allocation failed (coarse inverse)");
     CK(cudaMemcpyAsync(c->coarse_inv, inv.data(), sizeof(double) * inv.size(), cudaMemcpyHostToDevice, c->st));
     CK(cudaStreamSynchronize(c->st));
     c->coarse_n = n;
     c->coarse_ready = true;
+    c->coarse_version = c->op_version;
     return DG_OK;
 }
 
@@ -915,18 +919,55 @@ int dg_apply(dg_ctx* c, int level, int prec, const void* x, void* y) {
     return fail(DG_ERR_UNSUPPORTED, "precision not implemented");
 }
 
-int dg_estimate(dg_ctx* c, const double* u, const double* g_qp, const double* f_qp, const double* gD_qp,
-                double* eta2) {
+int dg_estimate_fiducial(dg_ctx* c, const dg_block* fiducial, int n_fiducial, const double* u, const double* g_qp,
+                         const double* f_qp, const double* gD_qp, double* eta2) {
     if (!c || !u || !eta2) return fail(DG_ERR_INVALID, "NULL argument");
-    if (!c->blocks.empty()) return fail(DG_ERR_UNSUPPORTED, "dg_estimate: single-box meshes only");
+    const int nbk = (int)c->blocks.size();
+    if (fiducial) {
+        if (nbk == 0) return fail(DG_ERR_INVALID, "a fiducial grid needs a multi-block mesh");
+        if (n_fiducial != nbk) return fail(DG_ERR_INVALID, "the fiducial grid must have one block per mesh block");
+        for (int b = 0; b < nbk; ++b)
+            if (fiducial[b].kind != c->blocks[b].kind ||
+                (fiducial[b].kind != DG_BLOCK_HEX8 && fiducial[b].face != c->blocks[b].face))
+                return fail(DG_ERR_INVALID, "fiducial block kinds and faces must be the mesh's");
+    }
     const int l = (int)c->lv.size() - 1;
     LevelDev& L = c->lv[l];
-    const long long nd = L.h.n_dofs();
+    const long long nd = L.h.n_dofs(), nm = L.h.n_mortar_pts, nb = L.h.n_bnd_pts;
+    const int nmort = (int)L.h.mortars.size();
     if (L.h.n_elems() == 0) return DG_OK;
-    double* X = nullptr;   // node coordinates (3 nd) and the apply's output (nd), stream-ordered
-    CK(cudaMallocAsync((void**)&X, sizeof(double) * 4 * nd, c->st));
-    double* y = X + 3 * nd;
-    cudaError_t e = launch_node_coords(geom_args(c, L), X, c->st);
+    // stream-ordered scratch: the apply's output (nd), node coordinates (3 nd, single box) or, with
+    // a fiducial grid, its mortar geometry (7 nm + nmort + 3 nb) and blocks
+    const size_t nfb = fiducial ? (sizeof(dg_block) * nbk + 7) / 8 : 0;
+    const size_t want = (size_t)nd + (nbk == 0 ? 3 * (size_t)nd : 0) +
+                        (fiducial ? 7 * (size_t)nm + nmort + 3 * (size_t)nb + nfb + 1 : 0);
+    double* S = nullptr;
+    CK(cudaMallocAsync((void**)&S, sizeof(double) * want, c->st));
+    double* y = S;
+    double* X = nbk == 0 ? y + nd : nullptr;
+    double *mgF = nullptr, *sigF = nullptr, *bxF = nullptr;
+    dg_block* fb = nullptr;
+    int* badF = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (fiducial) {
+        mgF = y + nd;
+        sigF = mgF + 7 * nm;
+        bxF = sigF + nmort;
+        fb = reinterpret_cast<dg_block*>(bxF + 3 * nb);
+        badF = reinterpret_cast<int*>(reinterpret_cast<double*>(fb) + nfb);
+        e = cudaMemcpyAsync(fb, fiducial, sizeof(dg_block) * nbk, cudaMemcpyHostToDevice, c->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(badF, 0, sizeof(int), c->st);
+        if (e == cudaSuccess) {
+            GeomArgs gF = geom_args(c, L);
+            gF.blocks = fb;
+            e = launch_mortar_geom(gF, nullptr, L.mortars, nmort, c->C, mgF, sigF, bxF, nb, badF, c->st);
+            c->launches += 1;
+        }
+    }
+    if (e == cudaSuccess && X) {
+        e = launch_node_coords(geom_args(c, L), X, c->st);
+        c->launches += 1;
+    }
     int rc = e == cudaSuccess ? apply_t<double>(c, l, u, y) : DG_OK;   // fills the trace buffer with u's traces
     if (e == cudaSuccess && rc == DG_OK) {
         EstimateArgs a{};
@@ -943,14 +984,32 @@ int dg_estimate(dg_ctx* c, const double* u, const double* g_qp, const double* f_
         a.tab = c->tab64;
         a.X = X;
         a.C = c->C;
+        a.n_blocks = nbk;
+        a.blocks = c->blocks_dev;
+        a.block = L.block;
+        a.leaves = L.leaves;
+        a.fblocks = fiducial ? fb : c->blocks_dev;
+        a.mgW = fiducial ? mgF : L.mg64;
+        a.sigW = fiducial ? sigF : L.sigma64;
         e = launch_estimate(a, u, g_qp, f_qp, gD_qp, eta2, c->st);
-        c->launches += 2;
+        c->launches += 1;
     }
-    cudaError_t ef = cudaFreeAsync(X, c->st);
+    int hbad = 0;
+    if (e == cudaSuccess && rc == DG_OK && badF) {
+        e = cudaMemcpyAsync(&hbad, badF, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    }
+    cudaError_t ef = cudaFreeAsync(S, c->st);
     if (e != cudaSuccess) return fail(DG_ERR_CUDA, cudaGetErrorString(e));
     if (rc != DG_OK) return rc;
     if (ef != cudaSuccess) return fail(DG_ERR_CUDA, cudaGetErrorString(ef));
+    if (hbad) return fail(DG_ERR_INVALID, "the fiducial grid folds an element (non-positive surface Jacobian)");
     return DG_OK;
+}
+
+int dg_estimate(dg_ctx* c, const double* u, const double* g_qp, const double* f_qp, const double* gD_qp,
+                double* eta2) {
+    return dg_estimate_fiducial(c, nullptr, 0, u, g_qp, f_qp, gD_qp, eta2);
 }
 
 int dg_convert(dg_ctx* c, int64_t n, int sp, const void* s, int dp, void* d) {

@@ -107,6 +107,7 @@ struct dg_ctx {
     double* coarse_inv = nullptr;   // dense inverse of the level-0 operator
     int coarse_n = 0;
     bool coarse_ready = false;
+    long long coarse_version = -1;  // op_version the coarse inverse belongs to
     bool has_zeroth = false;
     // puncture data on the finest level volume points
     double* p_alpha = nullptr;

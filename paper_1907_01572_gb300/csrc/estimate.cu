@@ -12,10 +12,16 @@
 // points: values I, first derivatives, and second derivatives (the first
 // derivative matrix times the LGL-node derivative matrix, exact because the
 // derivative of a degree-p polynomial is held by its LGL values).
+// On multi-block meshes the geometry is the exact block map (as in the
+// operator): J and X^k come from the map's first and second derivatives at
+// the GL points (blocks.h), composed with the element's linear map into its
+// block.  With a fiducial grid the integrands stay those of the physical grid
+// and the weights (w det J, w S), h_e, h_m and sigma are the fiducial grid's.
 // The mortar terms read the trace buffer that an FP64 apply of u leaves
 // behind: u and n_A . grad u of both sides at the mortar's GL points; each
 // element sums the mortars of its own slots, so every interior mortar counts
 // in full for both of its elements and the result needs no atomics.
+#include "blocks.h"
 #include "estimate.h"
 
 namespace dg {
@@ -89,12 +95,32 @@ __global__ void __launch_bounds__(kEstThreads) estimate_kernel(EstimateArgs a, c
         Mx[2][t] = s;
     }
     const double* M[3] = {Mx[0], Mx[1], Mx[2]};
-    const double* Xe = a.X + 3 * a.dof_off[e];
+    const double* Xe = a.n_blocks > 0 ? nullptr : a.X + 3 * a.dof_off[e];
     const double* ue = u + a.dof_off[e];
+    const bool blk = a.n_blocks > 0;
 
     // element diameter: largest distance between two of the eight vertices
     double he = 0.0;
-    if (threadIdx.x == 0) {
+    double binv = 1.0, bxi0[3] = {0.0, 0.0, 0.0};   // block meshes: xi_block = bxi0 + binv (xi + 1)
+    if (blk) {
+        const int* lf = a.leaves + 4 * e;
+        binv = 1.0 / (double)(1 << lf[0]);
+        for (int dd = 0; dd < 3; ++dd) bxi0[dd] = -1.0 + 2.0 * lf[1 + dd] * binv;
+    }
+    if (threadIdx.x == 0 && blk) {
+        const dg_block& BF = a.fblocks[a.block[e]];
+        double V[8][3];
+        for (int c = 0; c < 8; ++c) {
+            double xb[3];
+            for (int dd = 0; dd < 3; ++dd) xb[dd] = bxi0[dd] + binv * (((c >> dd) & 1) ? 2.0 : 0.0);
+            block_point(BF, xb, V[c]);
+        }
+        for (int c = 0; c < 8; ++c)
+            for (int d = c + 1; d < 8; ++d) {
+                const double dx = V[c][0] - V[d][0], dy = V[c][1] - V[d][1], dz = V[c][2] - V[d][2];
+                he = fmax(he, sqrt(dx * dx + dy * dy + dz * dz));
+            }
+    } else if (threadIdx.x == 0) {
         double V[8][3];
         for (int c = 0; c < 8; ++c) {
             const int idx = ((c & 1) ? n - 1 : 0) + n * (((c >> 1) & 1) ? n - 1 : 0) + n2 * (((c >> 2) & 1) ? n - 1 : 0);
@@ -107,14 +133,39 @@ __global__ void __launch_bounds__(kEstThreads) estimate_kernel(EstimateArgs a, c
             }
     }
 
-    // J_il = d x_i / d xi_l
-    double J[3][3];
-    for (int i = 0; i < 3; ++i) {
-        for (int t = threadIdx.x; t < n3; t += blockDim.x) F[t] = Xe[i * n3 + t];
-        __syncthreads();
-        J[i][0] = eval_at_point(F, T1, T2, M, 1, 0, 0, n, k);
-        J[i][1] = eval_at_point(F, T1, T2, M, 0, 1, 0, n, k);
-        J[i][2] = eval_at_point(F, T1, T2, M, 0, 0, 1, n, k);
+    // J_il = d x_i / d xi_l (and, on block meshes, the map's second derivatives Xs and the
+    // fiducial Jacobian determinant of the volume weight)
+    double J[3][3], Xs[3][3][3], detW = 0.0;
+    if (blk) {
+        double xp[3], xb[3] = {0.0, 0.0, 0.0};
+        const double* xg = a.tab + tab_n(TabIndex::GLx, n);
+        if (k < n3) {
+            const int ii[3] = {k % n, (k / n) % n, k / n2};
+            for (int dd = 0; dd < 3; ++dd) xb[dd] = bxi0[dd] + binv * (xg[ii[dd]] + 1.0);
+        }
+        const dg_block& B = a.blocks[a.block[e]];
+        block_jacobian(B, xb, J, xp);
+        block_hessian(B, xb, Xs);
+        for (int i = 0; i < 3; ++i)
+            for (int l = 0; l < 3; ++l) {
+                J[i][l] *= binv;
+                for (int m = 0; m < 3; ++m) Xs[i][l][m] *= binv * binv;
+            }
+        double JF[3][3];
+        block_jacobian(a.fblocks[a.block[e]], xb, JF, xp);
+        for (int i = 0; i < 3; ++i)
+            for (int l = 0; l < 3; ++l) JF[i][l] *= binv;
+        detW = JF[0][0] * (JF[1][1] * JF[2][2] - JF[1][2] * JF[2][1]) -
+               JF[0][1] * (JF[1][0] * JF[2][2] - JF[1][2] * JF[2][0]) +
+               JF[0][2] * (JF[1][0] * JF[2][1] - JF[1][1] * JF[2][0]);
+    } else {
+        for (int i = 0; i < 3; ++i) {
+            for (int t = threadIdx.x; t < n3; t += blockDim.x) F[t] = Xe[i * n3 + t];
+            __syncthreads();
+            J[i][0] = eval_at_point(F, T1, T2, M, 1, 0, 0, n, k);
+            J[i][1] = eval_at_point(F, T1, T2, M, 0, 1, 0, n, k);
+            J[i][2] = eval_at_point(F, T1, T2, M, 0, 0, 1, n, k);
+        }
     }
     double Ji[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}}, det = 1.0;
     if (k < n3) {
@@ -147,10 +198,17 @@ __global__ void __launch_bounds__(kEstThreads) estimate_kernel(EstimateArgs a, c
     double H[6];
     for (int c = 0; c < 6; ++c) H[c] = eval_at_point(F, T1, T2, M, kD[c][0], kD[c][1], kD[c][2], n, k);
     // minus sum_k (du/dx_k) X^k
-    for (int i = 0; i < 3; ++i) {
-        for (int t = threadIdx.x; t < n3; t += blockDim.x) F[t] = Xe[i * n3 + t];
-        __syncthreads();
-        for (int c = 0; c < 6; ++c) H[c] -= ux[i] * eval_at_point(F, T1, T2, M, kD[c][0], kD[c][1], kD[c][2], n, k);
+    if (blk) {
+        constexpr int kLM[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+        for (int i = 0; i < 3; ++i)
+            for (int c = 0; c < 6; ++c) H[c] -= ux[i] * Xs[i][kLM[c][0]][kLM[c][1]];
+    } else {
+        for (int i = 0; i < 3; ++i) {
+            for (int t = threadIdx.x; t < n3; t += blockDim.x) F[t] = Xe[i * n3 + t];
+            __syncthreads();
+            for (int c = 0; c < 6; ++c)
+                H[c] -= ux[i] * eval_at_point(F, T1, T2, M, kD[c][0], kD[c][1], kD[c][2], n, k);
+        }
     }
     double vol = 0.0;
     if (k < n3) {
@@ -162,7 +220,7 @@ __global__ void __launch_bounds__(kEstThreads) estimate_kernel(EstimateArgs a, c
         const long long vo = a.vqp_off[e];
         const double R = (f ? f[vo + k] : 0.0) * uv - (g ? g[vo + k] : 0.0) - lap;
         const double w = wg[k % n] * wg[(k / n) % n] * wg[k / n2];
-        vol = w * det * R * R;
+        vol = w * (blk ? detW : det) * R * R;
     }
     vol = block_sum(vol, red);
 
@@ -172,7 +230,7 @@ __global__ void __launch_bounds__(kEstThreads) estimate_kernel(EstimateArgs a, c
         const int mi = a.slot_mortar[s];
         const Mortar Mo = a.mortars[mi];
         const int q2 = Mo.q * Mo.q;
-        const double* mg = a.mg + 7 * Mo.goff;
+        const double* mg = a.mgW + 7 * Mo.goff;   // w S of the weighting grid
         const double* mt = a.mt + 4 * Mo.goff;
         double s1 = 0.0, s2 = 0.0;
         for (int pt = threadIdx.x; pt < q2; pt += blockDim.x) {
@@ -190,7 +248,7 @@ __global__ void __launch_bounds__(kEstThreads) estimate_kernel(EstimateArgs a, c
         s1 = block_sum(s1, red);
         s2 = block_sum(s2, red);
         if (threadIdx.x == 0) {
-            const double pm = Mo.q - 1, sig = a.sigma[mi];
+            const double pm = Mo.q - 1, sig = a.sigW[mi];
             const double hm = a.C * pm * pm / sig;
             mort += (Mo.eB >= 0 ? hm / pm * s1 : 0.0) + sig / hm * pm * pm * s2;
         }

@@ -17,8 +17,19 @@ struct EstimateArgs {
     const double* sigma;    // per mortar
     const double* mt;       // trace buffer of an FP64 apply of u: u_A, dn_A, u_B, dn_B per mortar point
     const double* tab;
-    const double* X;        // node coordinates, 3 n^3 per element at 3 dof_off[e]
+    const double* X;        // single box: node coordinates, 3 n^3 per element at 3 dof_off[e]
     double C;               // penalty constant of eq. (penaltyparameter)
+    // multi-block meshes: the exact block maps (J and second derivatives at the GL points)
+    int n_blocks;           // 0: single box (isoparametric geometry from X)
+    const dg_block* blocks; // device
+    const int* block;       // device, block of each element
+    const int* leaves;      // device, 4 per element
+    // fiducial grid (blocks of identical structure): volume weights and h_e from fblocks, mortar
+    // weights w S and sigma (hence h_m) from mgW / sigW; without one, fblocks = blocks, mgW = mg,
+    // sigW = sigma
+    const dg_block* fblocks;
+    const double* mgW;
+    const double* sigW;
 };
 
 // eta2[e] = h_e^2 p_e^2 ||f u - g - Lap u||^2_e + the mortar terms of the element.

@@ -113,6 +113,7 @@ _SIGS = {
     "dg_transfer": ([_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P], ctypes.c_int),
     "dg_smooth_static": ([_P, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.POINTER(dg_cheb_opts), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "dg_estimate": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "dg_estimate_fiducial": ([_P, _P, ctypes.c_int, _P, _P, _P, _P, _P], ctypes.c_int),
     "dg_hp_mark": ([ctypes.c_int, _P, _P, _P, _P, ctypes.POINTER(dg_amr_opts), _P, _P], ctypes.c_int),
     "dg_hp_refine": ([ctypes.c_int, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                       _P, _P, _P, _P], ctypes.c_int),
@@ -164,31 +165,33 @@ def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
+def block_array(blocks):
+    """ctypes array of dg_block from inputs-style block dicts."""
+    arr = (dg_block * len(blocks))()
+    kinds = {"hex8": DG_BLOCK_HEX8, "wedge": DG_BLOCK_WEDGE, "shell": DG_BLOCK_SHELL}
+    for i, b in enumerate(blocks):
+        arr[i].kind = kinds[b["kind"]]
+        if b["kind"] == "hex8":
+            for c in range(8):
+                for k in range(3):
+                    arr[i].corners[c][k] = float(b["corners"][c][k])
+        else:
+            arr[i].face = int(b["face"])
+        arr[i].a = float(b.get("a", 0.0))
+        arr[i].r = float(b.get("r", 0.0))
+        arr[i].r1 = float(b.get("r1", 0.0))
+        arr[i].r2 = float(b.get("r2", 0.0))
+    return arr
+
+
 def make_mesh_desc(desc):
     """dg_mesh_desc from an inputs-style dict (keeps the arrays alive on the struct).
     An optional "bc" entry gives the dg_bc_kind of each block face (6 per block)."""
     leaves = np.ascontiguousarray(np.asarray(desc["leaves"], dtype=np.int32).reshape(-1, 4))
     p = np.ascontiguousarray(np.asarray(desc["p"], dtype=np.int32).ravel())
     d = dg_mesh_desc()
-    if desc.get("bc") is not None:
-        bc = np.ascontiguousarray(np.asarray(desc["bc"], dtype=np.int32).ravel())
-        d.bc = bc.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
-        d._keep_bc = bc
     if desc.get("blocks"):
-        blocks = (dg_block * len(desc["blocks"]))()
-        kinds = {"hex8": DG_BLOCK_HEX8, "wedge": DG_BLOCK_WEDGE, "shell": DG_BLOCK_SHELL}
-        for i, b in enumerate(desc["blocks"]):
-            blocks[i].kind = kinds[b["kind"]]
-            if b["kind"] == "hex8":
-                for c in range(8):
-                    for k in range(3):
-                        blocks[i].corners[c][k] = float(b["corners"][c][k])
-            else:
-                blocks[i].face = int(b["face"])
-            blocks[i].a = float(b.get("a", 0.0))
-            blocks[i].r = float(b.get("r", 0.0))
-            blocks[i].r1 = float(b.get("r1", 0.0))
-            blocks[i].r2 = float(b.get("r2", 0.0))
+        blocks = block_array(desc["blocks"])
         eb = np.ascontiguousarray(np.asarray(desc["elem_block"], dtype=np.int32).ravel())
         d.n_blocks = len(desc["blocks"])
         d.blocks = ctypes.cast(blocks, ctypes.POINTER(dg_block))
@@ -197,6 +200,11 @@ def make_mesh_desc(desc):
         d.leaves = leaves.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
         d.p = p.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
         d._keep = (leaves, p, blocks, eb)
+    if desc.get("bc") is not None:
+        bc = np.ascontiguousarray(np.asarray(desc["bc"], dtype=np.int32).ravel())
+        d.bc = bc.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        d._keep_bc = bc
+    if desc.get("blocks"):
         return d
     for k in range(3):
         d.lo[k] = float(desc["lo"][k])
@@ -403,9 +411,15 @@ class Context:
         _check(lib().dg_rhs(self.h, _ptr(g_qp), _ptr(gD_qp), _ptr(F)))
         return F
 
-    def estimate(self, u, eta2, g_qp=None, f_qp=None, gD_qp=None):
-        """eta^2(e) of the finest level into eta2 (device double, n_elems)."""
-        _check(lib().dg_estimate(self.h, _ptr(u), _ptr(g_qp), _ptr(f_qp), _ptr(gD_qp), _ptr(eta2)))
+    def estimate(self, u, eta2, g_qp=None, f_qp=None, gD_qp=None, fiducial=None):
+        """eta^2(e) of the finest level into eta2 (device double, n_elems);
+        fiducial: block dicts of a fiducial grid (dg_estimate_fiducial) or None."""
+        if fiducial is None:
+            _check(lib().dg_estimate(self.h, _ptr(u), _ptr(g_qp), _ptr(f_qp), _ptr(gD_qp), _ptr(eta2)))
+        else:
+            arr = block_array(fiducial)
+            _check(lib().dg_estimate_fiducial(self.h, ctypes.cast(arr, ctypes.c_void_p), len(fiducial), _ptr(u),
+                                              _ptr(g_qp), _ptr(f_qp), _ptr(gD_qp), _ptr(eta2)))
         return eta2
 
     def smooth(self, b, x, level=-1, n_eigs=15, n_cheb=15, Lambda=20.0, want_lambda=True, lam_fixed=0.0):

@@ -107,15 +107,63 @@ def test_closed_forms_and_exact_solutions(torch):
     ctx.close()
 
 
-def test_block_meshes_are_rejected(torch):
+@pytest.mark.parametrize("name", ["blocks_turned_fine_side", "cubed_sphere_shell_2to1"])
+def test_estimator_on_block_meshes_matches_oracle(name, torch):
+    """Multi-block meshes (exact block maps and their second derivatives in
+    Lap u; turned interfaces, wedges and an inverse-radius shell with 2:1
+    faces): eta^2(e) within 1e-12 relative L2 (1e-10 per element) of the
+    oracle's, with and without the problem data."""
     from paper_1907_01572_gb300 import dgell
-    desc = CASES["blocks_turned_fine_side"]()
+    desc = CASES[name]()
+    m = oracle_mesh(desc)
     ctx = dgell.Context(desc)
-    n = ctx.level_info()["n_dofs"]
-    eta = torch.empty(ctx.level_info()["n_elems"], dtype=torch.float64, device="cuda")
+    u = inputs.random_vector(m.n_dofs, seed=22)
+    g, f, gD = _fields(ctx, torch)
+    eta = _estimate(ctx, torch.tensor(u, device="cuda"), torch, g, f, gD)
+    ref = estimator.estimate(m, u, g_fn=g_np, f_fn=f_np, gD_fn=gD_np, C=10.0)
+    assert rel_l2(eta, ref) < 1e-12
+    assert np.max(np.abs(eta - ref) / ref) < 1e-10
+    eta0 = _estimate(ctx, torch.tensor(u, device="cuda"), torch)
+    assert rel_l2(eta0, estimator.estimate(m, u, C=10.0)) < 1e-12
+    ctx.close()
+
+
+def test_fiducial_grid_estimator_matches_oracle(torch):
+    """The compactified cubed sphere (cube half-width 2, wedges to r = 10,
+    inverse-radius shell to r = 1e4) estimated on Problem C's fiducial grid
+    (cube of side 2/sqrt(3), wedges to r = 2, shell from 2 to 3): eta^2(e)
+    against the oracle's fiducial estimator; the fiducial weights change the
+    shell elements' eta^2 by orders of magnitude; mismatched fiducial blocks
+    are rejected."""
+    from paper_1907_01572_gb300 import dgell
+    desc = inputs.cubed_sphere_mesh(level=1, a=2.0, r=10.0, r_out=1e4, seed=4, pmin=2, pmax=4)
+    fid = inputs.cubed_sphere_blocks(a=1.0 / math.sqrt(3.0), r=2.0, r_out=3.0)
+    m = oracle_mesh(desc)
+    mf = m.with_blocks(fid)
+    ctx = dgell.Context(desc)
+    u = inputs.random_vector(m.n_dofs, seed=23)
+    # fields bounded out to r = 1e4: the Lorentzian's source and solution, f = 1 + 1 / (1 + r^2)
+    f_l = lambda x: 1.0 + 1.0 / (1.0 + np.sum(x * x, axis=1))
+    vxyz, bxyz = ctx.quadrature_points()
+    v, b = vxyz.T.cpu().numpy(), bxyz.T.cpu().numpy()
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a), device="cuda")
+    g, f, gD = dev(inputs.lorentzian_source(v)), dev(f_l(v)), dev(inputs.lorentzian_solution(b))
+    ud = torch.tensor(u, device="cuda")
+    eta = torch.empty(m.n_elems, dtype=torch.float64, device="cuda")
+    ctx.estimate(ud, eta, g_qp=g, f_qp=f, gD_qp=gD, fiducial=fid)
+    eta = eta.cpu().numpy()
+    ref = estimator.estimate(m, u, g_fn=inputs.lorentzian_source, f_fn=f_l, gD_fn=inputs.lorentzian_solution,
+                             C=10.0, fiducial=mf)
+    assert rel_l2(eta, ref) < 1e-12
+    assert np.max(np.abs(eta - ref) / ref) < 1e-10
+    phys = _estimate(ctx, ud, torch, g, f, gD)
+    shell = np.asarray(desc["elem_block"]) >= 7
+    assert np.median(phys[shell] / eta[shell]) > 1e3
+    bad = [dict(b) for b in fid]
+    bad[3] = dict(bad[3], kind="shell", face=bad[3]["face"], r1=2.0, r2=3.0)
     with pytest.raises(dgell.DgError) as ei:
-        ctx.estimate(torch.zeros(n, dtype=torch.float64, device="cuda"), eta)
-    assert ei.value.code == dgell.DG_ERR_UNSUPPORTED
+        ctx.estimate(ud, torch.empty_like(torch.tensor(eta, device="cuda")), fiducial=bad)
+    assert ei.value.code == dgell.DG_ERR_INVALID
     ctx.close()
 
 
