@@ -218,3 +218,30 @@ def test_constant_density_star_newton_matches_oracle():
     with pytest.raises(dgell.DgError):
         ctx.puncture_residual(torch.tensor(u, device="cuda"), R)
     ctx.close()
+
+
+def test_exact_coarse_solve_follows_the_zeroth_order_term():
+    """The V-cycle with the exact coarse solve (coarse = 1, a dense inverse of
+    the level-0 operator) equals the oracle's Cholesky V-cycle before and after
+    a zeroth-order term is set, and again after it changes: the inverse is
+    rebuilt for every new operator (as between Newton steps)."""
+    import torch
+    from paper_1907_01572_gb300 import dgell
+    desc = CASES["config1_affine_p3"]()
+    m = oracle_mesh(desc)
+    ctx = dgell.Context(desc)
+    vxyz, _ = ctx.quadrature_points()
+    X = vxyz.T.cpu().numpy()
+    f = inputs.random_vector(m.n_dofs, seed=71)
+    for scale in (None, 1.0, 5.0):
+        if scale is None:
+            H = multigrid.Hierarchy(m)
+        else:
+            coef = [scale * coef_fun(sipg.volume_points(m, e)) for e in range(m.n_elems)]
+            H = multigrid.Hierarchy(m, coef=coef)
+            ctx.set_zeroth_order(torch.tensor(scale * coef_fun(X), device="cuda"))
+        vo = H.vcycle(f, coarse="cholesky")
+        v = torch.empty(m.n_dofs, dtype=torch.float64, device="cuda")
+        ctx.vcycle(torch.tensor(f, device="cuda"), v, coarse=1)
+        assert rel_l2(v.cpu().numpy(), vo) < 1e-9, scale
+    ctx.close()
