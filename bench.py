@@ -25,11 +25,21 @@ sys.path.insert(0, ROOT)
 
 HBM_FALLBACK = 6800.0
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, ncu, every kernel of one FP32 apply of the
-# sweep mesh with per-bucket launches) keyed by the library version whose apply kernels were captured;
-# any other version reports null.  Versions 113-116 keep the apply kernels of 112.
-TRAFFIC_BYTES_PER_APPLY = {104: 1.3634e9, 105: 1.3709e9, 106: 1.3770e9, 108: 1.3775e9, 109: 1.3775e9,
-                           110: 1.3774e9, 112: 1.3770e9, 113: 1.3770e9, 114: 1.3770e9, 115: 1.3770e9,
-                           116: 1.3770e9, 118: 1.3154e9}
+# sweep mesh with per-bucket launches), keyed by a hash of the sources that define the apply kernels and
+# the data they read (kernels, launcher, packed records, geometry and mesh tables): any change to one of
+# them makes the entry miss and the bench report null until the counters are taken again.
+APPLY_SOURCES = ["apply_impl.cuh", "apply.h", "apply_f32.cu", "internal.h", "geom.cu", "geom.h", "host_mesh.cpp"]
+TRAFFIC_BYTES_PER_APPLY = {"3db6ad468e9b020c": 1.3154e9}   # library versions 118-120
+
+
+def apply_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in APPLY_SOURCES:
+        with open(os.path.join(ROOT, "paper_1907_01572_gb300", "csrc", f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def peaks():
@@ -397,8 +407,8 @@ def main():
                        "l2": "inputs larger than L2 (%.1f GB of inputs and outputs, metric terms ~0.4 GB)"
                              % (2 * 4 * N * R / 1e9), "parallelism": "replicas"},
             "roofline": {"bound": "hbm", "achieved": ach32, "peak": hbm, "unit": "GB/s", "frac": ach32 / hbm,
-                         "traffic": TRAFFIC_BYTES_PER_APPLY.get(dgell.dg_version()) if args.level == 5 else None,
-                         "peak_kind": peak_kind, "bytes_per_dof": b32,
+                         "traffic": TRAFFIC_BYTES_PER_APPLY.get(apply_source_hash()) if args.level == 5 else None,
+                         "peak_kind": peak_kind, "bytes_per_dof": b32, "apply_source_hash": apply_source_hash(),
                          "kernel": "dg_apply FP32: trace + element kernels of all degree buckets (one apply)"},
             "cpu_baseline": cpu,
             "e2e": {"value": ge2e, "unit": "GDOF/s", "h2d_bytes_per_step": N * 4 * Re, "d2h_bytes_per_step": N * 4 * Re,
