@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define DGELL_VERSION 120
+#define DGELL_VERSION 121
 
 enum {
     DG_OK = 0,

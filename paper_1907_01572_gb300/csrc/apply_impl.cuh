@@ -69,13 +69,20 @@ constexpr int r4(int v) { return (v + 3) & ~3; }
 // a + S1 b + S2 c.  The padding puts the 32 lanes of a pencil pass (one
 // x-, y- or z-pencil per lane) into distinct banks where the dense layout
 // does not: N = 8 (rows of 9, planes of 72; dense: 8-way conflicts along x,
-// 4-way along y), N = 4 (planes of 19) and N = 7 (planes of 52).
+// 4-way along y) and N = 7 (planes of 52).
 template <int N>
 struct Strides {
     static constexpr int S1 = N == 8 ? 9 : N;
     static constexpr int S2 = N == 8 ? 72 : (N == 7 ? 52 : N * N);
     static constexpr int SIZE = S2 * N;
 };
+
+// Stride of reference direction k (0, 1, 2) in the padded layout; a select
+// rather than a table, which a run-time index would put in local memory.
+template <int N>
+__device__ __forceinline__ int stride_of(int k) {
+    return k == 0 ? 1 : (k == 1 ? Strides<N>::S1 : Strides<N>::S2);
+}
 
 // Padded shared-memory index of the node with element-blocked index k.
 template <int N>
@@ -368,21 +375,37 @@ __device__ __forceinline__ void trace_slot(const LevelView<T>& L, const SlotInfo
         return;
     } else {
         constexpr int N2 = N * N, Q2 = Q * Q;
-        const int st[3] = {1, Strides<N>::S1, Strides<N>::S2};
         const int d = s.f >> 1, fn = (s.f & 1) ? N - 1 : 0;
         int t1, t2;
         tangential(d, t1, t2);
+        const int sdn = stride_of<N>(d), st1 = stride_of<N>(t1), st2 = stride_of<N>(t2);
+        const MortarMap<Q> toA(OR ? s.o : 0);
+        // this side's c at the lane's mortar points, loaded first so that they
+        // arrive while the two interpolation passes run
+        constexpr int QJ = (Q2 + 31) / 32;
+        T c1[QJ], c2[QJ], cn[QJ];
+#pragma unroll
+        for (int j = 0; j < QJ; ++j) {
+            const int kk = lane + 32 * j < Q2 ? lane + 32 * j : 0;
+            const int kA = OR ? toA(kk % Q, kk / Q) : kk;
+            c1[j] = co[t1 * Q2 + kA];
+            c2[j] = co[t2 * Q2 + kA];
+            cn[j] = co[d * Q2 + kA];
+        }
         T* uf = F;                  // u and n . grad_xi u at the N x N face nodes
         T* df = uf + N2;
         T* U1 = df + N2;            // u, d/dt1 u, dn u after the first tangential direction (Q x N)
         T* DU1 = U1 + Q * N;
         T* N1 = DU1 + Q * N;
-        for (int k = lane; k < N2; k += 32) {
+#pragma unroll
+        for (int k0 = 0; k0 < N2; k0 += 32) {   // unrolled: a lane's iterations overlap
+            const int k = k0 + lane;
+            if (k >= N2) continue;
             const int a = k % N, b = k / N;
-            const int base = a * st[t1] + b * st[t2];
+            const int base = a * st1 + b * st2;
             T v[N];
 #pragma unroll
-            for (int c = 0; c < N; ++c) v[c] = U[base + c * st[d]];
+            for (int c = 0; c < N; ++c) v[c] = U[base + c * sdn];
             T acc = 0;
 #pragma unroll
             for (int c = 0; c < N; ++c) acc += sDL[fn * N + c] * v[c];
@@ -391,7 +414,10 @@ __device__ __forceinline__ void trace_slot(const LevelView<T>& L, const SlotInfo
         }
         __syncwarp();
         const T* M1 = sFT + L.ft.off[N - kMinN][Q - kMinN][s.p0];
-        for (int k = lane; k < Q * N; k += 32) {
+#pragma unroll
+        for (int k0 = 0; k0 < Q * N; k0 += 32) {   // unrolled: a lane's iterations overlap
+            const int k = k0 + lane;
+            if (k >= Q * N) continue;
             const int i1 = k % Q, b = k / Q;
             T su = 0, sd = 0, sn = 0;
 #pragma unroll
@@ -410,8 +436,10 @@ __device__ __forceinline__ void trace_slot(const LevelView<T>& L, const SlotInfo
         __syncwarp();
         const T* M2 = sFT + L.ft.off[N - kMinN][Q - kMinN][s.p1];
         T* out = mt + 4 * s.goff + 2 * s.side * Q2;
-        const MortarMap<Q> toA(OR ? s.o : 0);
-        for (int k = lane; k < Q2; k += 32) {
+#pragma unroll
+        for (int k0 = 0; k0 < Q2; k0 += 32) {   // unrolled: a lane's iterations overlap
+            const int k = k0 + lane;
+            if (k >= Q2) continue;
             const int i1 = k % Q, i2 = k / Q, kA = OR ? toA(i1, i2) : k;
             T u = 0, g1 = 0, g2 = 0, gn = 0;
 #pragma unroll
@@ -425,7 +453,7 @@ __device__ __forceinline__ void trace_slot(const LevelView<T>& L, const SlotInfo
                 gn += iv * nb;
             }
             out[kA] = u;
-            out[Q2 + kA] = co[t1 * Q2 + kA] * g1 + co[t2 * Q2 + kA] * g2 + co[d * Q2 + kA] * gn;
+            out[Q2 + kA] = c1[k0 / 32] * g1 + c2[k0 / 32] * g2 + cn[k0 / 32] * gn;
         }
         __syncwarp();
     }
@@ -443,10 +471,10 @@ __device__ __forceinline__ void lift_apply(const LevelView<T>& L, const SlotInfo
         return;
     } else {
         constexpr int N2 = N * N, Q2 = Q * Q;
-        const int st[3] = {1, Strides<N>::S1, Strides<N>::S2};
         const int d = s.f >> 1, fn = (s.f & 1) ? N - 1 : 0;
         int t1, t2;
         tangential(d, t1, t2);
+        const int sdn = stride_of<N>(d), st1 = stride_of<N>(t1), st2 = stride_of<N>(t2);
         const T* PB1 = PA + Q2;
         const T* PB2 = PB1 + Q2;
         const T* PBn = PB2 + Q2;
@@ -454,7 +482,10 @@ __device__ __forceinline__ void lift_apply(const LevelView<T>& L, const SlotInfo
         T* X2 = X1 + Q * N;
         T* X3 = X2 + Q * N;
         const T* M2 = sFT + L.ft.off[N - kMinN][Q - kMinN][s.p1];
-        for (int k = lane; k < Q * N; k += 32) {
+#pragma unroll
+        for (int k0 = 0; k0 < Q * N; k0 += 32) {   // unrolled: a lane's iterations overlap
+            const int k = k0 + lane;
+            if (k >= Q * N) continue;
             const int i1 = k % Q, b = k / Q;
             T s1v = 0, s2v = 0, s3v = 0;
 #pragma unroll
@@ -471,7 +502,10 @@ __device__ __forceinline__ void lift_apply(const LevelView<T>& L, const SlotInfo
         }
         __syncwarp();
         const T* M1 = sFT + L.ft.off[N - kMinN][Q - kMinN][s.p0];
-        for (int k = lane; k < N2; k += 32) {
+#pragma unroll
+        for (int k0 = 0; k0 < N2; k0 += 32) {   // unrolled: a lane's iterations overlap
+            const int k = k0 + lane;
+            if (k >= N2) continue;
             const int a = k % N, b = k / N;
             T fu = 0, fd = 0;
 #pragma unroll
@@ -481,10 +515,10 @@ __device__ __forceinline__ void lift_apply(const LevelView<T>& L, const SlotInfo
                 fu += iv * X1[i1 + Q * b] + dv * X2[i1 + Q * b];
                 fd += iv * X3[i1 + Q * b];
             }
-            const int base = a * st[t1] + b * st[t2];
-            Y[base + fn * st[d]] += fu;
+            const int base = a * st1 + b * st2;
+            Y[base + fn * sdn] += fu;
 #pragma unroll
-            for (int c = 0; c < N; ++c) Y[base + c * st[d]] += sDL[fn * N + c] * fd;
+            for (int c = 0; c < N; ++c) Y[base + c * sdn] += sDL[fn * N + c] * fd;
         }
         __syncwarp();
     }
@@ -501,9 +535,8 @@ __device__ __forceinline__ void lift_slot(const LevelView<T>& L, const SlotInfo<
     if constexpr (Q < N) {
         return;
     } else {
-        constexpr int N2 = N * N, Q2 = Q * Q;
-        const int st[3] = {1, Strides<N>::S1, Strides<N>::S2};
-        const int d = s.f >> 1, fn = (s.f & 1) ? N - 1 : 0;
+        constexpr int Q2 = Q * Q;
+        const int d = s.f >> 1;
         int t1, t2;
         tangential(d, t1, t2);
         T* PA = F;              // flux factors at the Q x Q mortar points
@@ -515,7 +548,10 @@ __device__ __forceinline__ void lift_slot(const LevelView<T>& L, const SlotInfo<
         T* X3 = X2 + Q * N;
         const T sgn = s.side == 0 ? T(1) : T(-1);
         const MortarMap<Q> toA(OR ? s.o : 0);
-        for (int k = lane; k < Q2; k += 32) {
+#pragma unroll
+        for (int k0 = 0; k0 < Q2; k0 += 32) {   // unrolled: a lane's iterations overlap
+            const int k = k0 + lane;
+            if (k >= Q2) continue;
             const int kA = OR ? toA(k % Q, k / Q) : k;
             const T wS = wSp[kA];
             T uA = m[kA], dA = m[Q2 + kA];
@@ -796,15 +832,27 @@ __device__ __forceinline__ void element_body(const LevelView<T>& L, const ElemDe
         __syncwarp();
         {   // f = G g at the volume GL points (six stored values per point, read once: evict-first)
             const T* Ge = L.G + 6 * vo;
-            for (int k = lane; k < N3; k += 32) {
-                const int s = sidx<N>(k);
-                const T g0 = G1[s], g1 = G2[s], g2 = G3[s];
-                const T m00 = __ldcs(Ge + k), m01 = __ldcs(Ge + N3 + k), m02 = __ldcs(Ge + 2 * N3 + k);
-                const T m11 = __ldcs(Ge + 3 * N3 + k), m12 = __ldcs(Ge + 4 * N3 + k), m22 = __ldcs(Ge + 5 * N3 + k);
-                G1[s] = m00 * g0 + m01 * g1 + m02 * g2;
-                G2[s] = m01 * g0 + m11 * g1 + m12 * g2;
-                G3[s] = m02 * g0 + m12 * g1 + m22 * g2;
-                if (mass) A[s] = L.c0[vo + k] * A[s];   // the zeroth-order term, summed into A below
+            constexpr int GU = 4;   // points per lane whose metric terms are in flight together
+#pragma unroll 1
+            for (int k0 = lane; k0 < N3; k0 += 32 * GU) {
+                T m[GU][6];
+#pragma unroll
+                for (int u = 0; u < GU; ++u) {
+                    const int k = k0 + 32 * u < N3 ? k0 + 32 * u : k0;
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) m[u][c] = __ldcs(Ge + c * N3 + k);
+                }
+#pragma unroll
+                for (int u = 0; u < GU; ++u) {
+                    const int k = k0 + 32 * u;
+                    if (k >= N3) continue;
+                    const int s = sidx<N>(k);
+                    const T g0 = G1[s], g1 = G2[s], g2 = G3[s];
+                    G1[s] = m[u][0] * g0 + m[u][1] * g1 + m[u][2] * g2;
+                    G2[s] = m[u][1] * g0 + m[u][3] * g1 + m[u][4] * g2;
+                    G3[s] = m[u][2] * g0 + m[u][4] * g1 + m[u][5] * g2;
+                    if (mass) A[s] = L.c0[vo + k] * A[s];   // the zeroth-order term, summed into A below
+                }
             }
         }
         __syncwarp();
