@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define DGELL_VERSION 121
+#define DGELL_VERSION 122
 
 enum {
     DG_OK = 0,
@@ -193,6 +193,22 @@ int dg_quadrature_points(dg_ctx* ctx, int level, double* vol_xyz, double* bnd_xy
  * float for DG_FP32; DG_BF16: x bfloat16, y float); x and y must not
  * overlap.  Asynchronous. */
 int dg_apply(dg_ctx* ctx, int level, int prec, const void* x, void* y);
+
+/* dg_apply on nvec vectors held in HOST memory: y_r = L x_r, r < nvec (the
+ * operator of eq. (lh2) as for dg_apply).  hx: HOST, nvec input vectors of the
+ * level's n_dofs values each, back to back; hy: HOST, nvec outputs in the same
+ * layout; double for DG_FP64, float for DG_FP32 (DG_BF16: DG_ERR_UNSUPPORTED).
+ * The copy of vector r+1 to the device and of vector r-1 back run on two copy
+ * streams of the context while vector r is applied on its stream, through two
+ * device staging slots per direction that the context allocates on first use
+ * (4 n_dofs values of the precision, kept until dg_ctx_destroy; not counted by
+ * dg_ctx_footprint).  The host buffers should be page-locked (cudaHostAlloc or
+ * cudaHostRegister) for the copies to overlap the applies; pageable memory
+ * gives the same results.  Asynchronous: the context's stream waits for the
+ * last copy, so hy is complete once that stream is synchronised; hx and hy
+ * must stay untouched until then.  nvec = 0 does nothing.  Not for use
+ * inside stream capture (the first call allocates). */
+int dg_apply_host(dg_ctx* ctx, int level, int prec, int nvec, const void* hx, void* hy);
 
 /* Right-hand side F_h of eq. (equationFh2) on the finest level:
  * F = int g v - int_{Gamma_D} g_D n.grad v + int_{Gamma_D} sigma g_D v.

@@ -163,6 +163,53 @@ int apply_t(dg_ctx* c, int l, const T* x, T* y) {
     return DG_OK;
 }
 
+// dg_apply_host: vector r is copied in on hst[0], applied on the context's
+// stream and copied out on hst[1]; slot r % 2 of each direction is reused by
+// vector r + 2 once its apply (input slot) and its copy out (output slot) have
+// finished.  Event waits always refer to the latest record, made earlier in
+// host order.
+template <typename T>
+int apply_host_t(dg_ctx* c, int l, int nvec, const T* hx, T* hy) {
+    const long long n = c->lv[l].h.n_dofs();
+    const size_t vb = sizeof(T) * (size_t)n;
+    if (!c->hst[0]) {
+        for (int i = 0; i < 2; ++i) CK(cudaStreamCreateWithFlags(&c->hst[i], cudaStreamNonBlocking));
+        for (int s = 0; s < 2; ++s)
+            for (int k = 0; k < 3; ++k) CK(cudaEventCreateWithFlags(&c->hev[s][k], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c->hstart, cudaEventDisableTiming));
+    }
+    if (c->hstage_bytes < 4 * vb) {
+        CK(cudaStreamSynchronize(c->st));   // earlier calls may still read the old slots
+        if (c->hstage) CK(cudaFree(c->hstage));
+        c->hstage = nullptr;
+        c->hstage_bytes = 0;
+        CK(cudaMalloc(&c->hstage, 4 * vb));
+        c->hstage_bytes = 4 * vb;
+    }
+    T* dx[2] = {(T*)c->hstage, (T*)c->hstage + n};
+    T* dy[2] = {(T*)c->hstage + 2 * n, (T*)c->hstage + 3 * n};
+    CK(cudaEventRecord(c->hstart, c->st));   // the slots' earlier users on the context's stream
+    CK(cudaStreamWaitEvent(c->hst[0], c->hstart, 0));
+    CK(cudaStreamWaitEvent(c->hst[1], c->hstart, 0));
+    for (int r = 0; r < nvec; ++r) {
+        const int s = r & 1;
+        cudaEvent_t* ev = c->hev[s];   // [copied in, applied, copied out]
+        if (r >= 2) CK(cudaStreamWaitEvent(c->hst[0], ev[1], 0));
+        CK(cudaMemcpyAsync(dx[s], hx + (size_t)r * n, vb, cudaMemcpyHostToDevice, c->hst[0]));
+        CK(cudaEventRecord(ev[0], c->hst[0]));
+        CK(cudaStreamWaitEvent(c->st, ev[0], 0));
+        if (r >= 2) CK(cudaStreamWaitEvent(c->st, ev[2], 0));
+        const int rc = apply_t<T>(c, l, dx[s], dy[s]);
+        if (rc != DG_OK) return rc;
+        CK(cudaEventRecord(ev[1], c->st));
+        CK(cudaStreamWaitEvent(c->hst[1], ev[1], 0));
+        CK(cudaMemcpyAsync(hy + (size_t)r * n, dy[s], vb, cudaMemcpyDeviceToHost, c->hst[1]));
+        CK(cudaEventRecord(ev[2], c->hst[1]));
+    }
+    if (nvec > 0) CK(cudaStreamWaitEvent(c->st, c->hev[(nvec - 1) & 1][2], 0));   // copies out are in order
+    return DG_OK;
+}
+
 // Small coarse levels (at most kDenseMax DOFs): the solver applies the
 // assembled operator as a dense matrix-vector product -- one launch instead of
 // the latency-bound element pipeline.  The SIPG part is assembled once per
@@ -837,6 +884,13 @@ void dg_ctx_destroy(dg_ctx* c) {
     else cudaDeviceSynchronize();
     if (c->vgraph) cudaGraphExecDestroy(c->vgraph);
     apply_streams_destroy(c->as);
+    for (int i = 0; i < 2; ++i)
+        if (c->hst[i]) cudaStreamDestroy(c->hst[i]);
+    for (int sl = 0; sl < 2; ++sl)
+        for (int k = 0; k < 3; ++k)
+            if (c->hev[sl][k]) cudaEventDestroy(c->hev[sl][k]);
+    if (c->hstart) cudaEventDestroy(c->hstart);
+    if (c->hstage) cudaFree(c->hstage);
     c->arena.free_all();
     if (c->red_host) cudaFreeHost(c->red_host);
     delete c;
@@ -917,6 +971,18 @@ int dg_apply(dg_ctx* c, int level, int prec, const void* x, void* y) {
         return DG_OK;
     }
     return fail(DG_ERR_UNSUPPORTED, "precision not implemented");
+}
+
+int dg_apply_host(dg_ctx* c, int level, int prec, int nvec, const void* hx, void* hy) {
+    if (!c || nvec < 0) return fail(DG_ERR_INVALID, "NULL context or negative nvec");
+    if (nvec == 0) return DG_OK;
+    if (!hx || !hy) return fail(DG_ERR_INVALID, "NULL argument");
+    level = resolve_level(c, level);
+    if (level < 0 || level >= (int)c->lv.size()) return fail(DG_ERR_INVALID, "level out of range");
+    if (hx == hy) return fail(DG_ERR_INVALID, "hx and hy must not alias");
+    if (prec == DG_FP64) return apply_host_t<double>(c, level, nvec, (const double*)hx, (double*)hy);
+    if (prec == DG_FP32) return apply_host_t<float>(c, level, nvec, (const float*)hx, (float*)hy);
+    return fail(DG_ERR_UNSUPPORTED, "dg_apply_host: precision not implemented");
 }
 
 int dg_estimate_fiducial(dg_ctx* c, const dg_block* fiducial, int n_fiducial, const double* u, const double* g_qp,

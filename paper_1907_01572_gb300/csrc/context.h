@@ -130,6 +130,13 @@ struct dg_ctx {
     long long op_version = 0;       // bumped whenever operator coefficients change (zeroth-order term)
     long long launches = 0;
     dg::ApplyStreams as{};          // side streams of the per-bucket apply
+    // dg_apply_host: copy streams (in, out), per staging slot the events
+    // [copied in, applied, copied out], and the device staging slots
+    cudaStream_t hst[2] = {};
+    cudaEvent_t hev[2][3] = {};
+    cudaEvent_t hstart = nullptr;
+    void* hstage = nullptr;
+    size_t hstage_bytes = 0;
 };
 
 namespace dg {

@@ -97,6 +97,7 @@ _SIGS = {
     "dg_level_blocks": ([_P, ctypes.c_int, _P], ctypes.c_int),
     "dg_quadrature_points": ([_P, ctypes.c_int, _P, _P], ctypes.c_int),
     "dg_apply": ([_P, ctypes.c_int, ctypes.c_int, _P, _P], ctypes.c_int),
+    "dg_apply_host": ([_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P], ctypes.c_int),
     "dg_rhs": ([_P, _P, _P, _P], ctypes.c_int),
     "dg_smooth": ([_P, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.POINTER(dg_cheb_opts), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "dg_vcycle": ([_P, ctypes.c_int, _P, _P, ctypes.POINTER(dg_mg_opts)], ctypes.c_int),
@@ -406,6 +407,18 @@ class Context:
     def apply(self, x, y, level=-1):
         _check(lib().dg_apply(self.h, level, _prec(x), _ptr(x), _ptr(y)))
         return y
+
+    def apply_host(self, hx, hy, level=-1):
+        """hy[r] = L hx[r] for host tensors hx, hy of shape (nvec, n_dofs), float32 or
+        float64 (pinned for copy/apply overlap); complete once the context's stream
+        is synchronised (dg_apply_host)."""
+        if hx.device.type != "cpu" or hy.device.type != "cpu":
+            raise ValueError("apply_host takes host tensors")
+        if hx.dtype != hy.dtype or hx.shape != hy.shape or not (hx.is_contiguous() and hy.is_contiguous()):
+            raise ValueError("hx and hy must be contiguous host tensors of the same dtype and shape")
+        nvec = hx.shape[0] if hx.dim() == 2 else 1
+        _check(lib().dg_apply_host(self.h, level, _prec(hx), nvec, _ptr(hx), _ptr(hy)))
+        return hy
 
     def rhs(self, g_qp, gD_qp, F):
         _check(lib().dg_rhs(self.h, _ptr(g_qp), _ptr(gD_qp), _ptr(F)))
