@@ -29,7 +29,8 @@ HBM_FALLBACK = 6800.0
 # the data they read (kernels, launcher, packed records, geometry and mesh tables): any change to one of
 # them makes the entry miss and the bench report null until the counters are taken again.
 APPLY_SOURCES = ["apply_impl.cuh", "apply.h", "apply_f32.cu", "internal.h", "geom.cu", "geom.h", "host_mesh.cpp"]
-TRAFFIC_BYTES_PER_APPLY = {"3db6ad468e9b020c": 1.3154e9}   # library versions 118-120
+TRAFFIC_BYTES_PER_APPLY = {"3db6ad468e9b020c": 1.3154e9,    # library versions 118-120
+                           "0c7f8ffb426d0fae": 1.3316e9}    # versions 121-122: one capture per kernel
 
 
 def apply_source_hash():
