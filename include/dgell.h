@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define DGELL_VERSION 122
+#define DGELL_VERSION 123
 
 enum {
     DG_OK = 0,
@@ -271,7 +271,16 @@ typedef struct {
                           1: Schwarz smoother (Alg. 6) with element subdomains and no overlap:
                           n_schwarz cycles of r = b - J x, element-local CG on the element
                           diagonal blocks J_ee dx_e = r_e (all elements at once, to local_tol
-                          or local_iters steps), x += schwarz_omega dx */
+                          or local_iters steps), x += schwarz_omega dx;
+                          2: Schwarz smoother (Alg. 6) with overlapping subdomains, one per
+                          element: its nodes and the touching elements' nodes that coincide
+                          with its boundary nodes (one overlap layer), weights w_h of
+                          eq. (schwarz_weight) at zero overlap width (1, 1/2, 1/4, 1/8 inside,
+                          on faces, edges, corners), exact local solves with inverses of
+                          R_s J R_s^T built on first use (and after a change of the
+                          operator's coefficients); n_schwarz cycles of r = b - J x,
+                          x += sum_s R_s^T W_s (R_s J R_s^T)^-1 R_s r.  Levels with one degree
+                          and conforming faces only (else DG_ERR_UNSUPPORTED) */
     int n_schwarz;     /* <= 0 -> 3 (the paper's typical N_s) */
     int local_iters;   /* <= 0 -> 20 */
     double local_tol;  /* relative; <= 0 -> 1e-3 (the paper's local tolerance) */

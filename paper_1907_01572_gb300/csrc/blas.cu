@@ -647,4 +647,58 @@ template cudaError_t elem_cg_update<float>(float*, float*, float*, const float*,
 template cudaError_t elem_cg_update<double>(double*, double*, double*, const double*, const long long*, int,
                                             double*, cudaStream_t);
 
+// One CTA per subdomain: its residual entries gathered into shared memory, then
+// each thread forms rows of W_s A_s^-1 (R_s r), the inverse read a column at a
+// time across the threads.
+template <typename T>
+__global__ void ovl_local_kernel(const long long* __restrict__ sub_off, const long long* __restrict__ sub_dof,
+                                 const T* __restrict__ w, const long long* __restrict__ inv_off,
+                                 const T* __restrict__ inv, const T* __restrict__ r, T* __restrict__ u) {
+    extern __shared__ unsigned char ovl_smem[];
+    T* rs = reinterpret_cast<T*>(ovl_smem);
+    const int s = blockIdx.x;
+    const long long o = sub_off[s];
+    const int m = (int)(sub_off[s + 1] - o);
+    for (int j = threadIdx.x; j < m; j += blockDim.x) rs[j] = r[sub_dof[o + j]];
+    __syncthreads();
+    const T* A = inv + inv_off[s];
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        T acc = 0;
+        for (int k = 0; k < m; ++k) acc += A[(long long)k * m + j] * rs[k];
+        u[o + j] = w[o + j] * acc;
+    }
+}
+
+template <typename T>
+__global__ void ovl_gather_kernel(const long long* __restrict__ cof_off, const long long* __restrict__ cof,
+                                  const T* __restrict__ u, T* __restrict__ x, long long n) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T s = 0;
+    for (long long c = cof_off[i]; c < cof_off[i + 1]; ++c) s += u[cof[c]];
+    x[i] += s;
+}
+
+template <typename T>
+cudaError_t ovl_local(const long long* sub_off, const long long* sub_dof, const T* w, const long long* inv_off,
+                      const T* inv, const T* r, T* u, int n_sub, int max_m, cudaStream_t st) {
+    if (n_sub <= 0) return cudaSuccess;
+    ovl_local_kernel<T><<<n_sub, 256, (size_t)max_m * sizeof(T), st>>>(sub_off, sub_dof, w, inv_off, inv, r, u);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t ovl_gather(const long long* cof_off, const long long* cof, const T* u, T* x, long long n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    ovl_gather_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cof_off, cof, u, x, n);
+    return cudaGetLastError();
+}
+template cudaError_t ovl_local<double>(const long long*, const long long*, const double*, const long long*,
+                                       const double*, const double*, double*, int, int, cudaStream_t);
+template cudaError_t ovl_local<float>(const long long*, const long long*, const float*, const long long*,
+                                      const float*, const float*, float*, int, int, cudaStream_t);
+template cudaError_t ovl_gather<double>(const long long*, const long long*, const double*, double*, long long,
+                                        cudaStream_t);
+template cudaError_t ovl_gather<float>(const long long*, const long long*, const float*, float*, long long,
+                                       cudaStream_t);
+
 }  // namespace dg

@@ -82,6 +82,17 @@ template <typename T>
 cudaError_t elem_cg_update(T* dx, T* r, T* p, const T* Dp, const long long* dof_off, int ne, double* es,
                            cudaStream_t st);
 
+// Schwarz smoother with overlapping subdomains (Alg. 6): per subdomain s
+// (entries [sub_off[s], sub_off[s+1]), m of them), u = W_s A_s^-1 R_s r with
+// the stored inverse (column-major m x m at inv_off[s]); then, per global DOF
+// i, x_i += the sum of u over the entries ovl_cof[cof_off[i] .. cof_off[i+1])
+// in that order (deterministic).
+template <typename T>
+cudaError_t ovl_local(const long long* sub_off, const long long* sub_dof, const T* w, const long long* inv_off,
+                      const T* inv, const T* r, T* u, int n_sub, int max_m, cudaStream_t st);
+template <typename T>
+cudaError_t ovl_gather(const long long* cof_off, const long long* cof, const T* u, T* x, long long n, cudaStream_t st);
+
 template <typename T>
 cudaError_t axpby(T a, const T* x, T b, T* y, long long n, cudaStream_t st);   // y = a x + b y
 template <typename T>

@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <cstdlib>
 #include <string>
+#include <thread>
+#include <unordered_map>
 
 #include "context.h"
 #include "geom.h"
@@ -403,6 +405,42 @@ TransferView<T> tview(dg_ctx* c, int lc) {
     return t;
 }
 
+// Inverse of the symmetric part of the column-major n x n matrix h: Cholesky
+// L L^T, then the inverse column by column.  False if it is not positive definite.
+bool spd_inverse(const std::vector<double>& h, int n, std::vector<double>& inv) {
+    std::vector<double> M((size_t)n * n);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) M[(size_t)i * n + j] = 0.5 * (h[(size_t)i * n + j] + h[(size_t)j * n + i]);
+    std::vector<double> Lc((size_t)n * n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        double s = M[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k) s -= Lc[(size_t)j * n + k] * Lc[(size_t)j * n + k];
+        if (!(s > 0.0)) return false;
+        const double djj = std::sqrt(s);
+        Lc[(size_t)j * n + j] = djj;
+        for (int i = j + 1; i < n; ++i) {
+            double t = M[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k) t -= Lc[(size_t)i * n + k] * Lc[(size_t)j * n + k];
+            Lc[(size_t)i * n + j] = t / djj;
+        }
+    }
+    inv.assign((size_t)n * n, 0.0);
+    std::vector<double> z(n);
+    for (int col = 0; col < n; ++col) {
+        for (int i = 0; i < n; ++i) {
+            double t = (i == col) ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) t -= Lc[(size_t)i * n + k] * z[k];
+            z[i] = t / Lc[(size_t)i * n + i];
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            double t = z[i];
+            for (int k = i + 1; k < n; ++k) t -= Lc[(size_t)k * n + i] * inv[(size_t)col * n + k];
+            inv[(size_t)col * n + i] = t / Lc[(size_t)i * n + i];
+        }
+    }
+    return true;
+}
+
 // coarse-grid solve support: dense inverse of the level-0 operator (FP64),
 // assembled column by column with the matrix-free apply.
 // Dense inverse of the level-0 operator for the exact coarse solve, rebuilt
@@ -427,36 +465,8 @@ int ensure_coarse_inverse(dg_ctx* c) {
     CK(cudaStreamSynchronize(c->st));
     cudaFree(E);
     cudaFree(A);
-    // symmetric part, Cholesky L L^T, then the inverse column by column
-    std::vector<double> M((size_t)n * n);
-    for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j) M[(size_t)i * n + j] = 0.5 * (h[(size_t)i * n + j] + h[(size_t)j * n + i]);
-    std::vector<double> Lc((size_t)n * n, 0.0);
-    for (int j = 0; j < n; ++j) {
-        double s = M[(size_t)j * n + j];
-        for (int k = 0; k < j; ++k) s -= Lc[(size_t)j * n + k] * Lc[(size_t)j * n + k];
-        if (!(s > 0.0)) return fail(DG_ERR_BREAKDOWN, "level-0 operator is not positive definite");
-        const double djj = std::sqrt(s);
-        Lc[(size_t)j * n + j] = djj;
-        for (int i = j + 1; i < n; ++i) {
-            double t = M[(size_t)i * n + j];
-            for (int k = 0; k < j; ++k) t -= Lc[(size_t)i * n + k] * Lc[(size_t)j * n + k];
-            Lc[(size_t)i * n + j] = t / djj;
-        }
-    }
-    std::vector<double> inv((size_t)n * n, 0.0), z(n);
-    for (int col = 0; col < n; ++col) {
-        for (int i = 0; i < n; ++i) {
-            double t = (i == col) ? 1.0 : 0.0;
-            for (int k = 0; k < i; ++k) t -= Lc[(size_t)i * n + k] * z[k];
-            z[i] = t / Lc[(size_t)i * n + i];
-        }
-        for (int i = n - 1; i >= 0; --i) {
-            double t = z[i];
-            for (int k = i + 1; k < n; ++k) t -= Lc[(size_t)k * n + i] * inv[(size_t)col * n + k];
-            inv[(size_t)col * n + i] = t / Lc[(size_t)i * n + i];
-        }
-    }
+    std::vector<double> inv;
+    if (!spd_inverse(h, n, inv)) return fail(DG_ERR_BREAKDOWN, "level-0 operator is not positive definite");
     if (!c->coarse_inv) c->coarse_inv = c->arena.alloc<double>((size_t)n * n);   // level 0's size never changes
     if (!c->coarse_inv) return fail(DG_ERR_OOM, "device allocation failed (coarse inverse)");
     CK(cudaMemcpyAsync(c->coarse_inv, inv.data(), sizeof(double) * inv.size(), cudaMemcpyHostToDevice, c->st));
@@ -466,6 +476,10 @@ int ensure_coarse_inverse(dg_ctx* c) {
     c->coarse_version = c->op_version;
     return DG_OK;
 }
+
+// Alg. 6 with overlapping subdomains (defined below, after the geometry helpers).
+template <typename T>
+int smooth_overlap_t(dg_ctx* c, int l, const T* b, T* x, const dg_mg_opts* o);
 
 // Alg. 3: v = VCYCLE(f) on the finest level.
 template <typename T>
@@ -478,6 +492,7 @@ int vcycle_t(dg_ctx* c, const T* f, T* v, const dg_mg_opts* o) {
     if (o && o->coarse == 1 && (rc = ensure_coarse_inverse(c))) return rc;
     const dg_cheb_opts* co = o ? &o->cheb : nullptr;
     auto smooth = [&](int l, const T* b, T* x) {
+        if (o && o->smoother == 2) return smooth_overlap_t<T>(c, l, b, x, o);
         return (o && o->smoother == 1) ? smooth_schwarz_t<T>(c, l, b, x, o) : smooth_t<T>(c, l, b, x, co);
     };
     auto F = [&](int l) -> const T* { return l == Lt ? f : work_of<T>(c->lv[l]).f; };
@@ -586,6 +601,313 @@ GeomArgs geom_args(dg_ctx* c, const LevelDev& L) {
     g.blocks = c->blocks_dev;
     g.block = L.block;
     return g;
+}
+
+// ---- Alg. 6 with overlapping subdomains --------------------------------------
+// Subdomain of element e_c: its own nodes plus every other element's node at
+// the position of one of e_c's boundary nodes (the touching elements'
+// coinciding DG nodes: one overlap layer, of zero width).  A node's weight is
+// w_h of eq. (schwarz_weight) at vanishing overlap width, evaluated at the
+// e_c node it sits on: 1 inside, 1/2 on a face, 1/4 on an edge, 1/8 on a
+// corner.  The local operator R_s J R_s^T is read off the level operator's
+// element blocks, which are probed with the matrix-free FP64 apply (elements
+// two or more faces apart share a probe), and inverted exactly.  Levels with
+// one degree and conforming faces only.
+struct CellKey {
+    long long i, j, k;
+    bool operator==(const CellKey& o) const { return i == o.i && j == o.j && k == o.k; }
+};
+struct CellHash {
+    size_t operator()(const CellKey& c) const {
+        return (size_t)(c.i * 73856093LL) ^ (size_t)(c.j * 19349663LL) ^ (size_t)(c.k * 83492791LL);
+    }
+};
+
+int ensure_overlap(dg_ctx* c, int l) {
+    LevelDev& L = c->lv[l];
+    if (L.ovl_version == c->op_version) return DG_OK;
+    const LevelHost& h = L.h;
+    const int ne = h.n_elems();
+    const int pdeg = h.p[0];
+    for (int e = 0; e < ne; ++e)
+        if (h.p[e] != pdeg)
+            return fail(DG_ERR_UNSUPPORTED, "overlapping Schwarz subdomains need one degree on every element of a level");
+    std::vector<std::vector<int>> nbr(ne);
+    for (const Mortar& m : h.mortars) {
+        if (m.eB < 0) continue;
+        if (h.leaves[4 * m.eA] != h.leaves[4 * m.eB])
+            return fail(DG_ERR_UNSUPPORTED, "overlapping Schwarz subdomains need conforming faces (no 2:1 faces)");
+        nbr[m.eA].push_back(m.eB);
+        nbr[m.eB].push_back(m.eA);
+    }
+    const int n = pdeg + 1, n3 = n * n * n;
+    const long long N = h.n_dofs();
+    const std::vector<long long>& off = h.dof_off;
+    auto elem_of = [&](long long d) { return (int)(std::upper_bound(off.begin(), off.end(), d) - off.begin()) - 1; };
+    auto nbound = [&](int k) {
+        const int ix[3] = {k % n, (k / n) % n, k / (n * n)};
+        int b = 0;
+        for (int a = 0; a < 3; ++a) b += (ix[a] == 0 || ix[a] == n - 1);
+        return b;
+    };
+    const bool first = (L.sub_off == nullptr);
+    std::vector<long long> sub_off, sub_dof;
+    std::vector<double> wts;
+    if (first) {
+        // node positions
+        std::vector<double> X(3 * (size_t)N);
+        double* Xd = nullptr;
+        CK(cudaMalloc(&Xd, sizeof(double) * 3 * (size_t)N));
+        cudaError_t ce = launch_node_coords(geom_args(c, L), Xd, c->st);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(X.data(), Xd, sizeof(double) * X.size(), cudaMemcpyDeviceToHost, c->st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->st);
+        cudaFree(Xd);
+        if (ce != cudaSuccess) return fail(DG_ERR_CUDA, std::string("overlap subdomains: ") + cudaGetErrorString(ce));
+        auto pos = [&](long long d, double P[3]) {
+            const int e = elem_of(d);
+            const long long k = d - off[e];
+            for (int a = 0; a < 3; ++a) P[a] = X[3 * off[e] + a * n3 + k];
+        };
+        double xmax = 1.0;
+        for (double v : X) xmax = std::max(xmax, std::fabs(v));
+        const double q = 1e-9 * xmax;   // cell size of the position hash
+        auto cell = [&](const double P[3]) {
+            return CellKey{(long long)std::floor(P[0] / q), (long long)std::floor(P[1] / q), (long long)std::floor(P[2] / q)};
+        };
+        std::vector<int> bnd;   // boundary nodes of an element
+        for (int k = 0; k < n3; ++k)
+            if (nbound(k) > 0) bnd.push_back(k);
+        std::unordered_map<CellKey, std::vector<long long>, CellHash> cells;
+        for (int e = 0; e < ne; ++e)
+            for (int k : bnd) {
+                double P[3];
+                pos(off[e] + k, P);
+                cells[cell(P)].push_back(off[e] + k);
+            }
+        sub_off.push_back(0);
+        for (int e = 0; e < ne; ++e) {
+            for (int k = 0; k < n3; ++k) {
+                sub_dof.push_back(off[e] + k);
+                wts.push_back(std::ldexp(1.0, -nbound(k)));
+            }
+            std::vector<std::pair<long long, int>> contact;   // (global DOF, e_c node it sits on)
+            for (int k : bnd) {
+                double P[3];
+                pos(off[e] + k, P);
+                const double tol = 1e-9 * std::max(1.0, std::sqrt(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]));
+                const CellKey c0 = cell(P);
+                for (int di = -1; di <= 1; ++di)
+                    for (int dj = -1; dj <= 1; ++dj)
+                        for (int dk = -1; dk <= 1; ++dk) {
+                            auto it = cells.find(CellKey{c0.i + di, c0.j + dj, c0.k + dk});
+                            if (it == cells.end()) continue;
+                            for (long long d : it->second) {
+                                if (d >= off[e] && d < off[e] + n3) continue;
+                                double Q[3];
+                                pos(d, Q);
+                                const double dx = Q[0] - P[0], dy = Q[1] - P[1], dz = Q[2] - P[2];
+                                if (std::sqrt(dx * dx + dy * dy + dz * dz) <= tol) contact.push_back({d, k});
+                            }
+                        }
+            }
+            std::sort(contact.begin(), contact.end());
+            for (const auto& ct : contact) {
+                sub_dof.push_back(ct.first);
+                wts.push_back(std::ldexp(1.0, -nbound(ct.second)));
+            }
+            sub_off.push_back((long long)sub_dof.size());
+        }
+    } else {   // the subdomains stay; only the operator changed
+        sub_off.resize(ne + 1);
+        CK(cudaMemcpyAsync(sub_off.data(), L.sub_off, sizeof(long long) * (ne + 1), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        sub_dof.resize(sub_off.back());
+        CK(cudaMemcpyAsync(sub_dof.data(), L.sub_dof, sizeof(long long) * sub_dof.size(), cudaMemcpyDeviceToHost,
+                           c->st));
+        CK(cudaStreamSynchronize(c->st));
+    }
+    const long long E = sub_off.back();
+    int max_m = 0;
+    long long inv_total = 0;
+    std::vector<long long> inv_off(ne + 1, 0);
+    for (int e = 0; e < ne; ++e) {
+        const long long m = sub_off[e + 1] - sub_off[e];
+        max_m = std::max(max_m, (int)m);
+        inv_off[e + 1] = inv_off[e] + m * m;
+    }
+    inv_total = inv_off[ne];
+    if ((double)inv_total * 12.0 > 8e9)
+        return fail(DG_ERR_UNSUPPORTED, "overlapping Schwarz: local inverses would take more than 8 GB");
+    // element blocks J(e2, e) for e2 = e and its face neighbours (column-major n3 x n3:
+    // row = node of e2, column = node of e), probed colour by colour: a colour holds
+    // elements at least three faces apart, so their columns do not overlap
+    std::vector<int> color(ne, -1), mark(ne + 1, -1);
+    int ncol = 0;
+    for (int e = 0; e < ne; ++e) {
+        std::vector<char> used;
+        auto forbid = [&](int x) {
+            if (color[x] >= 0) {
+                if ((int)used.size() <= color[x]) used.resize(color[x] + 1, 0);
+                used[color[x]] = 1;
+            }
+        };
+        for (int a : nbr[e]) {
+            forbid(a);
+            for (int b2 : nbr[a]) forbid(b2);
+        }
+        int cc = 0;
+        while (cc < (int)used.size() && used[cc]) ++cc;
+        color[e] = cc;
+        ncol = std::max(ncol, cc + 1);
+    }
+    std::unordered_map<long long, size_t> boff;
+    size_t nblk = 0;
+    for (int e = 0; e < ne; ++e) {
+        boff[(long long)e * ne + e] = (nblk++) * (size_t)n3 * n3;
+        for (int a : nbr[e]) boff[(long long)a * ne + e] = (nblk++) * (size_t)n3 * n3;
+    }
+    if ((double)nblk * n3 * n3 * 8.0 > 8e9)
+        return fail(DG_ERR_UNSUPPORTED, "overlapping Schwarz: element blocks would take more than 8 GB of host memory");
+    std::vector<double> blk(nblk * (size_t)n3 * n3);
+    {
+        std::vector<std::vector<int>> by_color(ncol);
+        for (int e = 0; e < ne; ++e) by_color[color[e]].push_back(e);
+        double *xd = nullptr, *yd = nullptr;
+        CK(cudaMalloc(&xd, sizeof(double) * N));
+        CK(cudaMalloc(&yd, sizeof(double) * N));
+        std::vector<double> xh(N, 0.0), yh(N);
+        int rc = DG_OK;
+        cudaError_t ce = cudaSuccess;
+        for (int cc = 0; cc < ncol && rc == DG_OK && ce == cudaSuccess; ++cc)
+            for (int a = 0; a < n3 && rc == DG_OK && ce == cudaSuccess; ++a) {
+                for (int e : by_color[cc]) xh[off[e] + a] = 1.0;
+                ce = cudaMemcpyAsync(xd, xh.data(), sizeof(double) * N, cudaMemcpyHostToDevice, c->st);
+                if (ce == cudaSuccess) rc = apply_t<double>(c, l, xd, yd);
+                if (ce == cudaSuccess && rc == DG_OK)
+                    ce = cudaMemcpyAsync(yh.data(), yd, sizeof(double) * N, cudaMemcpyDeviceToHost, c->st);
+                if (ce == cudaSuccess && rc == DG_OK) ce = cudaStreamSynchronize(c->st);
+                for (int e : by_color[cc]) {
+                    xh[off[e] + a] = 0.0;
+                    auto put = [&](int e2) {
+                        double* B = &blk[boff[(long long)e2 * ne + e]];
+                        for (int i = 0; i < n3; ++i) B[i + (size_t)a * n3] = yh[off[e2] + i];
+                    };
+                    put(e);
+                    for (int e2 : nbr[e]) put(e2);
+                }
+            }
+        cudaFree(xd);
+        cudaFree(yd);
+        if (rc != DG_OK) return rc;
+        if (ce != cudaSuccess) return fail(DG_ERR_CUDA, std::string("overlap blocks: ") + cudaGetErrorString(ce));
+    }
+    // local operators and their inverses, subdomains split over the host cores
+    std::vector<double> inv(inv_total);
+    std::vector<int> bad(ne, 0);
+    auto work = [&](int e0, int e1) {
+        std::vector<double> A, Ai;
+        for (int e = e0; e < e1; ++e) {
+            const long long o = sub_off[e];
+            const int m = (int)(sub_off[e + 1] - o);
+            std::vector<int> el(m), lo(m);
+            for (int j = 0; j < m; ++j) {
+                el[j] = elem_of(sub_dof[o + j]);
+                lo[j] = (int)(sub_dof[o + j] - off[el[j]]);
+            }
+            A.assign((size_t)m * m, 0.0);
+            for (int k = 0; k < m; ++k)
+                for (int j = 0; j < m; ++j) {
+                    auto it = boff.find((long long)el[j] * ne + el[k]);
+                    if (it != boff.end()) A[(size_t)k * m + j] = blk[it->second + lo[j] + (size_t)lo[k] * n3];
+                }
+            if (!spd_inverse(A, m, Ai)) {
+                bad[e] = 1;
+                continue;
+            }
+            std::copy(Ai.begin(), Ai.end(), inv.begin() + inv_off[e]);
+        }
+    };
+    {
+        const int nt = std::max(1, std::min((int)std::thread::hardware_concurrency(), 32));
+        std::vector<std::thread> th;
+        for (int t = 0; t < nt; ++t) th.emplace_back(work, (int)((long long)ne * t / nt), (int)((long long)ne * (t + 1) / nt));
+        for (auto& t : th) t.join();
+    }
+    for (int e = 0; e < ne; ++e)
+        if (bad[e]) return fail(DG_ERR_BREAKDOWN, "overlapping Schwarz: a local operator is not positive definite");
+    std::vector<float> inv32(inv.begin(), inv.end());
+    Arena& Ar = c->arena;
+    if (first) {
+        // per global DOF, the subdomain entries that hold it, in entry order
+        std::vector<long long> cof_off(N + 1, 0), cof(E);
+        for (long long t = 0; t < E; ++t) ++cof_off[sub_dof[t] + 1];
+        for (long long i = 0; i < N; ++i) cof_off[i + 1] += cof_off[i];
+        std::vector<long long> fill(cof_off.begin(), cof_off.end() - 1);
+        for (long long t = 0; t < E; ++t) cof[fill[sub_dof[t]]++] = t;
+        std::vector<float> w32(wts.begin(), wts.end());
+        L.sub_off = Ar.upload(sub_off, c->st);
+        L.sub_dof = Ar.upload(sub_dof, c->st);
+        L.inv_off = Ar.upload(inv_off, c->st);
+        L.ovl_cof_off = Ar.upload(cof_off, c->st);
+        L.ovl_cof = Ar.upload(cof, c->st);
+        L.ovl_w64 = Ar.upload(wts, c->st);
+        L.ovl_w32 = Ar.upload(w32, c->st);
+        L.ovl_inv64 = Ar.alloc<double>(inv_total);
+        L.ovl_inv32 = Ar.alloc<float>(inv_total);
+        L.ovl_u64 = Ar.alloc<double>(E);
+        L.ovl_u32 = Ar.alloc<float>(E);
+        if (Ar.failed) return fail(DG_ERR_OOM, "device allocation failed (overlapping Schwarz)");
+        L.ovl_max_m = max_m;
+        CK(cudaStreamSynchronize(c->st));   // the host vectors above go out of scope
+    }
+    CK(cudaMemcpyAsync(L.ovl_inv64, inv.data(), sizeof(double) * inv.size(), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(L.ovl_inv32, inv32.data(), sizeof(float) * inv32.size(), cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    L.ovl_version = c->op_version;
+    return DG_OK;
+}
+
+template <typename T>
+const T* ovl_w(const LevelDev& L);
+template <>
+const double* ovl_w<double>(const LevelDev& L) { return L.ovl_w64; }
+template <>
+const float* ovl_w<float>(const LevelDev& L) { return L.ovl_w32; }
+template <typename T>
+const T* ovl_inv(const LevelDev& L);
+template <>
+const double* ovl_inv<double>(const LevelDev& L) { return L.ovl_inv64; }
+template <>
+const float* ovl_inv<float>(const LevelDev& L) { return L.ovl_inv32; }
+template <typename T>
+T* ovl_u(LevelDev& L);
+template <>
+double* ovl_u<double>(LevelDev& L) { return L.ovl_u64; }
+template <>
+float* ovl_u<float>(LevelDev& L) { return L.ovl_u32; }
+
+// Alg. 6 with overlapping subdomains: n_schwarz cycles of r = b - J x,
+// x += sum_s R_s^T W_s (R_s J R_s^T)^-1 R_s r.
+template <typename T>
+int smooth_overlap_t(dg_ctx* c, int l, const T* b, T* x, const dg_mg_opts* o) {
+    int rc = ensure_work<T>(c, l);
+    if (rc) return rc;
+    if ((rc = ensure_dense(c, l))) return rc;
+    if ((rc = ensure_overlap(c, l))) return rc;
+    LevelDev& L = c->lv[l];
+    const int ns = o->n_schwarz > 0 ? o->n_schwarz : 3;
+    Work<T>& W = work_of<T>(L);
+    const long long n = L.h.n_dofs();
+    cudaStream_t st = c->st;
+    for (int s = 0; s < ns; ++s) {
+        if ((rc = solver_apply<T>(c, l, x, W.Ap))) return rc;
+        CK(sub3<T>(b, W.Ap, W.r, n, st));
+        CK(ovl_local<T>(L.sub_off, L.sub_dof, ovl_w<T>(L), L.inv_off, ovl_inv<T>(L), W.r, ovl_u<T>(L), L.h.n_elems(),
+                        L.ovl_max_m, st));
+        CK(ovl_gather<T>(L.ovl_cof_off, L.ovl_cof, ovl_u<T>(L), x, n, st));
+        c->launches += 3;
+    }
+    return DG_OK;
 }
 
 int upload_level(dg_ctx* c, LevelDev& L, int li, std::string& err) {

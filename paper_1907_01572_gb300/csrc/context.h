@@ -50,6 +50,17 @@ struct LevelDev {
     int *leaves = nullptr, *p = nullptr, *block = nullptr;
     int oriented = 0;                 // some mortar has a turned side B (block interfaces)
     double* schwarz_es = nullptr;     // element-local CG scalars of the Schwarz smoother (3 per element)
+    // Schwarz smoother with overlapping subdomains (one per element): entries
+    // [sub_off[s], sub_off[s+1]) hold the subdomain's global DOFs and weights;
+    // the inverse of its local operator (column-major, m x m) starts at
+    // inv_off[s]; per global DOF, ovl_cof_off / ovl_cof list the entries that
+    // hold it (for a fixed-order sum of the local corrections)
+    long long *sub_off = nullptr, *sub_dof = nullptr, *inv_off = nullptr;
+    long long *ovl_cof_off = nullptr, *ovl_cof = nullptr;
+    double *ovl_w64 = nullptr, *ovl_inv64 = nullptr, *ovl_u64 = nullptr;
+    float *ovl_w32 = nullptr, *ovl_inv32 = nullptr, *ovl_u32 = nullptr;
+    int ovl_max_m = 0;
+    long long ovl_version = -1;       // op_version the local inverses belong to
     long long *dof_off = nullptr, *vqp_off = nullptr;
     Mortar* mortars = nullptr;
     int *slot_off = nullptr, *slot_mortar = nullptr;
