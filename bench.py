@@ -271,6 +271,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--served", type=int, default=96, help="requests of the served stream to serve (512 in all)")
+    ap.add_argument("--compactified", action="store_true",
+                    help="also solve the star on the cubed sphere with the shell to r = 1e9 (level 3, p = 3, overlapping Schwarz)")
     ap.add_argument("--full-configs", action="store_true",
                     help="also solve configs 3 and 4 at their stated sizes (several minutes)")
     args = ap.parse_args()
@@ -392,6 +394,8 @@ def main():
         solve = solve_bench(dgell, inputs, torch, n_served=args.served)
     if args.full_configs and rank == 0:
         solve = dict(solve or {}, full_size=full_configs(dgell, inputs, torch))
+    if args.compactified and rank == 0:
+        solve = dict(solve or {}, compactified_shell=compactified_config(dgell, inputs, torch))
     flops = info["apply_flops"]
 
     if rank == 0:
@@ -452,6 +456,9 @@ SERVED_RATE_HZ = 2.2   # 70 % of the 3.1 solves/s this mix sustains on 4 slots (
 # Jacobian) cost the served mix far more than it saved (capacity 0.46 against 3.0 solves/s).  The
 # library's defaults stay the paper's.
 SPHERE_MG = dict(n_eigs=35, n_cheb=10, coarse=1)
+# V-cycle of the star with the inverse-radius shell out to r = 1e9 (one degree, conforming faces): the
+# Schwarz smoother with overlapping subdomains, exact local and coarse solves
+OVERLAP_MG = dict(smoother=2, coarse=1, n_schwarz=3)
 
 
 def solve_bench(dgell, inputs, torch, n_solves=8, n_served=96, n_cap=32):
@@ -459,8 +466,10 @@ def solve_bench(dgell, inputs, torch, n_solves=8, n_served=96, n_cap=32):
     FP64 V-cycle and with the FP32 V-cycle, each V-cycle replayed as a CUDA graph
     on a dedicated stream: the 4^3 p=3 Poisson problem and the star with a
     density jump on the 13-block cubed sphere (centre cube a = 2, wedges to
-    r = 10, inverse-radius shell to r = 20, closed-form Dirichlet data); then
-    the two-puncture Newton solve on the same kind of cubed sphere."""
+    r = 10, inverse-radius shell to r = 20, closed-form Dirichlet data), and
+    the same star on a uniform p = 4 sphere with the shell out to r = 1e9
+    (overlapping Schwarz smoother); then the two-puncture Newton solve on the
+    same kind of cubed sphere."""
     import numpy as np
     out = {}
     stream = torch.cuda.Stream()
@@ -470,6 +479,9 @@ def solve_bench(dgell, inputs, torch, n_solves=8, n_served=96, n_cap=32):
          None, n_solves, {}),
         ("star_cubed_sphere", inputs.star_sphere_mesh(level=2, refine=1, r_out=20.0), inputs.star_source,
          inputs.star_solution, 3, SPHERE_MG),
+        ("star_compactified_sphere_overlap",
+         inputs.star_sphere_mesh(level=2, refine=0, p_cut=4, p_lo=4, p_hi=4, r_out=1e9), inputs.star_source,
+         inputs.star_solution, 3, OVERLAP_MG),
     ]
     with torch.cuda.stream(stream):
         for name, desc, g, gD, n_case, mg in cases:
@@ -545,6 +557,47 @@ def solve_bench(dgell, inputs, torch, n_solves=8, n_served=96, n_cap=32):
         _, s = serve.Server(slots=4, mg_prec=prec).run(burst)
         cap[pname] = {k: s[k] for k in ("requests", "wall_s", "solves_per_s", "p50_ms", "p99_ms")}
     out["served_capacity"] = cap
+    return out
+
+
+def compactified_config(dgell, inputs, torch, level=3, p=3):
+    """The density-jump star on config 3's domain as stated: the 13-block cubed
+    sphere with the inverse-radius shell out to r = 1e9, every block at `level`
+    with one degree p (the overlapping Schwarz smoother needs one degree and
+    conforming faces), closed-form Dirichlet data at r = 1e9.  One warm-up
+    solve (subdomain setup, plan tuning, graph capture), then a timed one, with
+    the FP32 and the FP64 V-cycle, to 1e-10."""
+    out = {}
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        desc = inputs.star_sphere_mesh(level=level, refine=0, p_cut=p, p_lo=p, p_hi=p, r_out=1e9)
+        ctx = dgell.Context(desc)
+        info = ctx.level_info()
+        xyz, bxyz = ctx.quadrature_points()
+        gq = torch.tensor(inputs.star_source(xyz.T.cpu().numpy()), device="cuda")
+        gd = torch.tensor(inputs.star_solution(bxyz.T.cpu().numpy()), device="cuda")
+        F = torch.empty(info["n_dofs"], dtype=torch.float64, device="cuda")
+        ctx.rhs(gq, gd, F)
+        out = {"n_dofs": info["n_dofs"], "n_elems": info["n_elems"], "levels": info["n_levels"], "p": p,
+               "blocks": len(desc["blocks"]), "r_out": 1e9, "mg_opts": OVERLAP_MG}
+        sols = {}
+        for pname, prec in (("mixed_fp32_vcycle", dgell.DG_FP32), ("fp64", dgell.DG_FP64)):
+            for s in range(2):
+                x = torch.zeros_like(F)
+                stream.synchronize()
+                t = time.perf_counter()
+                st = ctx.solve(F, x, tol=1e-10, max_iter=300, mg_prec=prec, **OVERLAP_MG)
+                stream.synchronize()
+                dt = time.perf_counter() - t
+                if s == 0:
+                    out[pname + "_first_solve_s"] = dt   # includes the subdomain setup
+            sols[pname] = x
+            out[pname] = {"seconds": dt, "solves_per_s": 1.0 / dt, "iterations": st["iterations"],
+                          "rel_residual": st["rel_residual"]}
+        out["device_gb"] = ctx.level_info()["device_bytes"] / 1e9
+        out["mixed_vs_fp64_rel_l2"] = float((sols["mixed_fp32_vcycle"] - sols["fp64"]).norm() / sols["fp64"].norm())
+        ctx.close()
+    stream.synchronize()
     return out
 
 

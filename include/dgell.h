@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define DGELL_VERSION 123
+#define DGELL_VERSION 124
 
 enum {
     DG_OK = 0,
@@ -294,7 +294,9 @@ int dg_vcycle(dg_ctx* ctx, int prec, const void* f, void* v, const dg_mg_opts* o
  * DG_FP32: FP32 V-cycle inside the FP64 Krylov loop, i.e. mixed precision).
  * b, x: device double, n_dofs; x holds the initial guess on entry.  Stops
  * when ||b - J x||_2 <= tol ||b||_2 (recursive residual, confirmed with a
- * true FP64 residual at exit) or after max_iter iterations. */
+ * true FP64 residual: while the true one is still above tol, FCG restarts
+ * from x with r = b - J x, at most 3 times) or after max_iter iterations in
+ * all. */
 typedef struct {
     double tol;        /* relative residual target; <= 0 -> 1e-10 */
     int max_iter;      /* N_iter,FCG; <= 0 -> 100 */

@@ -814,11 +814,20 @@ int ensure_overlap(dg_ctx* c, int l) {
                 el[j] = elem_of(sub_dof[o + j]);
                 lo[j] = (int)(sub_dof[o + j] - off[el[j]]);
             }
+            // runs of entries on one element (own nodes first, then contacts by DOF)
+            std::vector<int> run0;
+            for (int j = 0; j < m; ++j)
+                if (j == 0 || el[j] != el[j - 1]) run0.push_back(j);
+            run0.push_back(m);
             A.assign((size_t)m * m, 0.0);
-            for (int k = 0; k < m; ++k)
-                for (int j = 0; j < m; ++j) {
-                    auto it = boff.find((long long)el[j] * ne + el[k]);
-                    if (it != boff.end()) A[(size_t)k * m + j] = blk[it->second + lo[j] + (size_t)lo[k] * n3];
+            for (size_t rk = 0; rk + 1 < run0.size(); ++rk)
+                for (size_t rj = 0; rj + 1 < run0.size(); ++rj) {
+                    auto it = boff.find((long long)el[run0[rj]] * ne + el[run0[rk]]);
+                    if (it == boff.end()) continue;
+                    const double* B = &blk[it->second];
+                    for (int k = run0[rk]; k < run0[rk + 1]; ++k)
+                        for (int j = run0[rj]; j < run0[rj + 1]; ++j)
+                            A[(size_t)k * m + j] = B[lo[j] + (size_t)lo[k] * n3];
                 }
             if (!spd_inverse(A, m, Ai)) {
                 bad[e] = 1;
@@ -1492,60 +1501,72 @@ int dg_solve(dg_ctx* c, const double* b, double* x, const dg_solver_opts* o, dg_
     double rr;
     if ((rc = read_out(1, &rr))) return rc;
     CK(cudaMemsetAsync(c->fcg, 0, sizeof(FcgState), st));
-    int k = 0;
+    int k = 0, restarts = 0;
     double rel = nb > 0 ? std::sqrt(rr) / nb : 0.0;
     int status = DG_OK;
-    while (k < maxit && rel >= tol && nb > 0) {
-        // v = VCYCLE(r)
-        if (!use_mg) {
-            CK(cudaMemcpyAsync(v, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-        } else {
-            if (mgp == DG_FP32) {
-                CK(cast_d2f(r, c->fcg32[0], n, st));
-                c->launches += 1;
+    double true_rel = 0.0;
+    for (;;) {
+        int j = 0;   // iterations since the (re)start
+        while (k < maxit && rel >= tol && nb > 0) {
+            // v = VCYCLE(r)
+            if (!use_mg) {
+                CK(cudaMemcpyAsync(v, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+            } else {
+                if (mgp == DG_FP32) {
+                    CK(cast_d2f(r, c->fcg32[0], n, st));
+                    c->launches += 1;
+                }
+                if ((rc = vcycle_maybe_graph(c, mgp, r, v, mo, o ? o->graph_mode : 0))) return rc;
+                if (mgp == DG_FP32) {
+                    CK(cast_f2d(c->fcg32[1], v, n, st));
+                    c->launches += 1;
+                }
             }
-            if ((rc = vcycle_maybe_graph(c, mgp, r, v, mo, o ? o->graph_mode : 0))) return rc;
-            if (mgp == DG_FP32) {
-                CK(cast_f2d(c->fcg32[1], v, n, st));
-                c->launches += 1;
+            if ((rc = apply_t<double>(c, Lt, v, w))) return rc;
+            {
+                const double* a[3] = {v, v, v};
+                const double* bb[3] = {r, w, q};
+                CK(dots<double>(a, bb, j == 0 ? 2 : 3, n, c->red, st));
             }
+            CK(fcg_scalars(c->fcg, c->red.out, j, st));
+            if (j == 0) {
+                CK(cudaMemcpyAsync(d, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(q, w, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+            } else {
+                CK(fcg_dq(c->fcg, d, q, v, w, n, st));
+            }
+            CK(fcg_update(c->fcg, x, r, d, q, n, c->red, st));
+            c->launches += 6;
+            if ((rc = read_out(1, &rr))) return rc;
+            FcgState fs;
+            CK(cudaMemcpyAsync(&fs, c->fcg, sizeof(FcgState), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            ++k;
+            ++j;
+            if (fs.breakdown || !std::isfinite(rr)) {
+                status = DG_ERR_BREAKDOWN;
+                break;
+            }
+            rel = std::sqrt(rr) / nb;
         }
-        if ((rc = apply_t<double>(c, Lt, v, w))) return rc;
+        // true residual
+        if ((rc = apply_t<double>(c, Lt, x, t))) return rc;
+        CK(sub3<double>(b, t, w, n, st));
         {
-            const double* a[3] = {v, v, v};
-            const double* bb[3] = {r, w, q};
-            CK(dots<double>(a, bb, k == 0 ? 2 : 3, n, c->red, st));
+            const double* a[1] = {w};
+            CK(dots<double>(a, a, 1, n, c->red, st));
         }
-        CK(fcg_scalars(c->fcg, c->red.out, k, st));
-        if (k == 0) {
-            CK(cudaMemcpyAsync(d, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-            CK(cudaMemcpyAsync(q, w, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-        } else {
-            CK(fcg_dq(c->fcg, d, q, v, w, n, st));
-        }
-        CK(fcg_update(c->fcg, x, r, d, q, n, c->red, st));
-        c->launches += 6;
-        if ((rc = read_out(1, &rr))) return rc;
-        FcgState fs;
-        CK(cudaMemcpyAsync(&fs, c->fcg, sizeof(FcgState), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        ++k;
-        if (fs.breakdown || !std::isfinite(rr)) {
-            status = DG_ERR_BREAKDOWN;
-            break;
-        }
-        rel = std::sqrt(rr) / nb;
+        double tr2;
+        if ((rc = read_out(1, &tr2))) return rc;
+        true_rel = nb > 0 ? std::sqrt(tr2) / nb : 0.0;
+        // on an ill-conditioned system the recursive residual can drift below the
+        // true one: restart FCG from x with r = b - J x (at most 3 times)
+        if (status != DG_OK || !(true_rel >= tol) || k >= maxit || restarts >= 3 || nb == 0) break;
+        CK(cudaMemcpyAsync(r, w, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemsetAsync(c->fcg, 0, sizeof(FcgState), st));
+        rel = true_rel;
+        ++restarts;
     }
-    // true residual
-    if ((rc = apply_t<double>(c, Lt, x, t))) return rc;
-    CK(sub3<double>(b, t, w, n, st));
-    {
-        const double* a[1] = {w};
-        CK(dots<double>(a, a, 1, n, c->red, st));
-    }
-    double tr2;
-    if ((rc = read_out(1, &tr2))) return rc;
-    const double true_rel = nb > 0 ? std::sqrt(tr2) / nb : 0.0;
     if (status == DG_OK && rel >= tol && nb > 0) status = DG_ERR_NOT_CONVERGED;
     if (stats) {
         stats->iterations = k;

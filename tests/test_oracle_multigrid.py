@@ -280,3 +280,26 @@ def test_overlap_one_layer_step_weights_and_conforming_only():
     lv = inputs.refine(inputs.uniform_leaves(1), lambda lf: lf == (1, 0, 0, 0))
     with pytest.raises(ValueError):
         multigrid.overlap_subdomains(Mesh((0, 0, 0), (1, 1, 1), lv, [2] * len(lv)), 1)
+
+
+def test_overlap_one_layer_partition_of_unity_and_single_element():
+    """One overlap layer on a conforming box: the weights of all subdomains
+    holding a DOF add up to 1 wherever the DOF's position is not on the domain
+    boundary (a node on a face, edge or corner is shared by 2, 4 or 8 elements,
+    each weighting it 1/2, 1/4 or 1/8), and on a single element one cycle from
+    x = 0 is W A^-1 b (its subdomain is the element itself)."""
+    m = Mesh((0, 0, 0), (1, 1, 1), inputs.uniform_leaves(1), [2] * 8)
+    subs = multigrid.overlap_subdomains(m, 1)
+    tot = np.zeros(m.n_dofs)
+    for d, W in subs:
+        np.add.at(tot, d, W)
+    X = np.vstack([m.node_coords(e) for e in range(m.n_elems)])
+    inner = np.all((X > 1e-12) & (X < 1 - 1e-12), axis=1)
+    assert inner.sum() > 0 and np.allclose(tot[inner], 1.0, atol=1e-14)
+    assert np.all(tot[~inner] < 1.0)
+    one = Mesh((0, 0, 0), (1, 1, 1), [(0, 0, 0, 0)], [3])
+    A = sipg.assemble(one, 10.0)
+    (d, W), = multigrid.overlap_subdomains(one, 1)
+    b = np.random.default_rng(4).standard_normal(one.n_dofs)
+    x = multigrid.overlap_schwarz_smoother(A, [(d, W)], np.zeros_like(b), b, n_cycles=1)
+    assert np.allclose(x, W * np.linalg.solve(A.toarray(), b), rtol=1e-10, atol=1e-12)
