@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define DGELL_VERSION 124
+#define DGELL_VERSION 125
 
 enum {
     DG_OK = 0,

@@ -663,9 +663,18 @@ __global__ void ovl_local_kernel(const long long* __restrict__ sub_off, const lo
     __syncthreads();
     const T* A = inv + inv_off[s];
     for (int j = threadIdx.x; j < m; j += blockDim.x) {
-        T acc = 0;
-        for (int k = 0; k < m; ++k) acc += A[(long long)k * m + j] * rs[k];
-        u[o + j] = w[o + j] * acc;
+        // four partial sums so that four loads of the (streamed, read-once-per-
+        // cycle) inverse are in flight per thread
+        T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        int k = 0;
+        for (; k + 4 <= m; k += 4) {
+            a0 += __ldcs(A + (long long)k * m + j) * rs[k];
+            a1 += __ldcs(A + (long long)(k + 1) * m + j) * rs[k + 1];
+            a2 += __ldcs(A + (long long)(k + 2) * m + j) * rs[k + 2];
+            a3 += __ldcs(A + (long long)(k + 3) * m + j) * rs[k + 3];
+        }
+        for (; k < m; ++k) a0 += __ldcs(A + (long long)k * m + j) * rs[k];
+        u[o + j] = w[o + j] * ((a0 + a1) + (a2 + a3));
     }
 }
 
