@@ -1,9 +1,11 @@
 """hp-adaptive solve loop (Sec. II.D): solve, estimate, mark, refine.
 
-Each step builds a context on the current single-box mesh, solves
--Lap u + f u = g (u = g_D on the boundary) with dg_solve, computes eta^2(e)
-with dg_estimate, applies Algorithm 4 with dg_hp_mark and refines the leaf
-set with dg_hp_refine (2:1 balanced).  The compute is entirely in libdgell
+Each step builds a context on the current mesh (a single box or a
+multi-block mesh), solves -Lap u + f u = g (u = g_D on the boundary) with
+dg_solve, computes eta^2(e) with dg_estimate (or dg_estimate_fiducial),
+applies Algorithm 4 with dg_hp_mark and refines the leaf set with
+dg_hp_refine or dg_hp_refine_mesh (2:1 balanced, across block interfaces
+too).  The compute is entirely in libdgell
 (CUDA kernels for the solve and the estimator, host C++ for marking and
 refinement); this module sequences the calls and evaluates the caller's
 problem functions at the quadrature points the library reports.
@@ -28,12 +30,15 @@ def _values(fn, pts):
 
 def adapt(desc, g_fn, gD_fn=None, f_fn=None, steps=3, theta=0.2, criterion=dgell.DG_MARK_FRACTION,
           gamma_h=0.25, gamma_p=0.1, p_max=8, pred_init=math.inf, tol=1e-10, max_iter=200, mg_prec=dgell.DG_FP64,
-          penalty_c=10.0, keep_solution=False):
+          penalty_c=10.0, keep_solution=False, fiducial=None):
     """Runs `steps` solve-estimate-refine cycles (plus the final solve and
-    estimate) from the mesh description `desc` (inputs-style dict, single
-    box).  Returns one record per mesh: n_elems, n_dofs, iterations,
-    rel_residual, eta2 (host array), action (host array, None on the last
-    mesh) and desc; with keep_solution=True also u (host array)."""
+    estimate) from the mesh description `desc` (inputs-style dict: a single
+    box, refined with dg_hp_refine, or a multi-block mesh, refined with
+    dg_hp_refine_mesh; fiducial: the blocks of a fiducial grid for the
+    estimator, multi-block meshes only).  Returns one record per mesh:
+    n_elems, n_dofs, iterations, rel_residual, eta2 (host array), action
+    (host array, None on the last mesh) and desc; with keep_solution=True
+    also u (host array)."""
     import torch
     desc = dict(desc)
     leaves = np.asarray(desc["leaves"], dtype=np.int32).reshape(-1, 4)
@@ -56,7 +61,7 @@ def adapt(desc, g_fn, gD_fn=None, f_fn=None, steps=3, theta=0.2, criterion=dgell
             u = torch.zeros_like(F)
             st = ctx.solve(F, u, tol=tol, max_iter=max_iter, mg_prec=mg_prec)
             eta = torch.empty(info["n_elems"], dtype=torch.float64, device="cuda")
-            ctx.estimate(u, eta, g_qp=g, f_qp=f, gD_qp=gD)
+            ctx.estimate(u, eta, g_qp=g, f_qp=f, gD_qp=gD, fiducial=fiducial)
             eta2 = eta.cpu().numpy()
             rec = dict(n_elems=info["n_elems"], n_dofs=info["n_dofs"], iterations=st["iterations"],
                        rel_residual=st["rel_residual"], eta2=eta2, action=None,
@@ -70,5 +75,10 @@ def adapt(desc, g_fn, gD_fn=None, f_fn=None, steps=3, theta=0.2, criterion=dgell
             break
         act, nxt = dgell.hp_mark(eta2, pred, p, leaves[:, 0], criterion, theta, gamma_h, gamma_p, p_max)
         rec["action"] = act
-        leaves, p, pred, _ = dgell.hp_refine(leaves, p, act, nxt, pred_init=pred_init)
+        if desc.get("blocks"):
+            desc, pred, _ = dgell.hp_refine_mesh(desc, act, nxt, pred_init=pred_init)
+            leaves = np.asarray(desc["leaves"], dtype=np.int32).reshape(-1, 4)
+            p = np.asarray(desc["p"], dtype=np.int32).ravel()
+        else:
+            leaves, p, pred, _ = dgell.hp_refine(leaves, p, act, nxt, pred_init=pred_init)
     return history

@@ -229,3 +229,33 @@ def test_hp_adaptive_loop(torch):
     assert sums[-1] < 0.25 * sums[0], sums
     assert errs[-1] < 0.25 * errs[0], errs
     assert hist[-1]["n_dofs"] > hist[0]["n_dofs"]
+
+
+def test_hp_adaptive_loop_on_a_block_mesh(torch):
+    """The adaptive loop on the 13-block cubed sphere (shell to r = 20, every
+    block at level 1, p = 2) with the steep front inside it: every mesh is
+    solved to 1e-10, the marking on the GPU's eta^2 equals the oracle's, the
+    leaf set is refined across block interfaces (dg_hp_refine_mesh), and the
+    summed estimator and the L2 error against the closed form fall."""
+    from paper_1907_01572_gb300 import amr
+    desc = inputs.cubed_sphere_mesh(level=1, a=2.0, r=10.0, r_out=20.0, seed=0, pmin=2, pmax=2)
+    hist = amr.adapt(desc, g_fn=lambda x: _front(x, torch)[1], gD_fn=lambda x: _front(x, torch)[0],
+                     steps=2, theta=0.3, keep_solution=True)
+    assert len(hist) == 3
+    errs, sums = [], []
+    for h in hist:
+        assert h["rel_residual"] < 1e-10
+        m = oracle_mesh(h["desc"])
+        errs.append(sipg.l2_error(m, h["u"], lambda x: _front(x.T, np)[0]))
+        sums.append(h["eta2"].sum())
+    # the first marking (predictions all infinite) against the oracle's
+    h = hist[0]
+    lvl = np.asarray(h["desc"]["leaves"])[:, 0]
+    marked = hpamr.mark(list(h["eta2"]), 'fraction', 0.3)
+    act, _ = hpamr.smooth_pred(list(h["eta2"]), [math.inf] * len(lvl), list(h["desc"]["p"]), list(lvl), marked,
+                               0.25, 0.1)
+    assert h["action"].tolist() == act
+    assert hist[-1]["n_dofs"] > hist[0]["n_dofs"]
+    assert len(np.asarray(hist[-1]["desc"]["elem_block"])) == hist[-1]["n_elems"]
+    assert sums[-1] < sums[0], sums
+    assert errs[-1] < errs[0], errs
