@@ -411,6 +411,8 @@ def main():
             "roofline": {"bound": "hbm", "achieved": ach32, "peak": hbm, "unit": "GB/s", "frac": ach32 / hbm,
                          "traffic": TRAFFIC_BYTES_PER_APPLY.get(apply_source_hash()) if args.level == 5 else None,
                          "peak_kind": peak_kind, "bytes_per_dof": b32, "apply_source_hash": apply_source_hash(),
+                         # the stricter vector-only figure: read x and write y once (8 B/DOF in FP32)
+                         "frac_vec": N * R * 8 / (ms32 * 1e-3) / 1e9 / hbm,
                          "kernel": "dg_apply FP32: trace + element kernels of all degree buckets (one apply)"},
             "cpu_baseline": cpu,
             "e2e": {"value": ge2e, "unit": "GDOF/s", "h2d_bytes_per_step": N * 4 * Re, "d2h_bytes_per_step": N * 4 * Re,
