@@ -463,6 +463,34 @@ SPHERE_MG = dict(n_eigs=35, n_cheb=10, coarse=1)
 OVERLAP_MG = dict(smoother=2, coarse=1, n_schwarz=3)
 
 
+def l2_error_closed_form(dgell, torch, desc, u, u_fn):
+    """||u_h - u||_2 (eq. l2norm) by the operator's own GL quadrature, from
+    library calls only: u_h^T M u_h - 2 u_h^T F(u) + sum F(u^2), with M u_h the
+    difference of two applies (with and without the zeroth-order term f = 1)
+    and F(g) = dg_rhs of g (sum_i phi_i = 1).  None if any call fails."""
+    try:
+        ctx = dgell.Context(desc)
+        try:
+            xyz, _ = ctx.quadrature_points()
+            ue = torch.tensor(u_fn(xyz.T.cpu().numpy()), dtype=torch.float64, device="cuda")
+            Lu = torch.empty_like(u)
+            ctx.apply(u, Lu)
+            ctx.set_zeroth_order(torch.ones_like(ue))
+            LMu = torch.empty_like(u)
+            ctx.apply(u, LMu)
+            F1 = torch.empty_like(u)
+            ctx.rhs(ue, None, F1)
+            F2 = torch.empty_like(u)
+            ctx.rhs(ue * ue, None, F2)
+            torch.cuda.current_stream().synchronize()
+            e2 = float(u @ (LMu - Lu)) - 2.0 * float(u @ F1) + float(F2.sum())
+            return max(e2, 0.0) ** 0.5
+        finally:
+            ctx.close()
+    except Exception:
+        return None
+
+
 def solve_bench(dgell, inputs, torch, n_solves=8, n_served=96, n_cap=32):
     """Linear solves to 1e-10 relative residual (FP64 outer FCG) with the plain
     FP64 V-cycle and with the FP32 V-cycle, each V-cycle replayed as a CUDA graph
@@ -497,6 +525,8 @@ def solve_bench(dgell, inputs, torch, n_solves=8, n_served=96, n_cap=32):
             res = {"n_dofs": info["n_dofs"], "n_elems": info["n_elems"], "levels": info["n_levels"], "mg_opts": mg}
             if desc.get("blocks"):
                 res["blocks"] = len(desc["blocks"])
+            exact = gD if gD is not None else (
+                lambda X: np.sin(np.pi * X[:, 0]) * np.sin(np.pi * X[:, 1]) * np.sin(np.pi * X[:, 2]))
             for pname, prec in (("fp64", dgell.DG_FP64), ("mixed_fp32_vcycle", dgell.DG_FP32)):
                 lat, its, rr = [], [], []
                 for s in range(n_case + 2):
@@ -511,7 +541,8 @@ def solve_bench(dgell, inputs, torch, n_solves=8, n_served=96, n_cap=32):
                         its.append(st["iterations"])
                         rr.append(st["rel_residual"])
                 r = _latency(lat)
-                r.update({"iterations": its[-1], "max_rel_residual": max(rr)})
+                r.update({"iterations": its[-1], "max_rel_residual": max(rr),
+                          "l2_error_vs_closed_form": l2_error_closed_form(dgell, torch, desc, x, exact)})
                 res[pname] = r
             out[name] = res
             ctx.close()
