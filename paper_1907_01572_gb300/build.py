@@ -27,7 +27,20 @@ def sources():
 
 
 def build(verbose=False, force=False):
+    """Builds (or finds up to date) libdgell.so.  Processes that build at the
+    same time (parallel test workers) take turns through a lock file, and the
+    later ones find the library already fresh."""
+    import fcntl
     os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as lk:
+        fcntl.flock(lk, fcntl.LOCK_EX)
+        try:
+            return _build_locked(verbose, force)
+        finally:
+            fcntl.flock(lk, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose, force):
     srcs = sources()
     deps = (srcs + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
             + [os.path.join(HERE, "..", "include", "dgell.h")])
