@@ -611,7 +611,7 @@ GeomArgs geom_args(dg_ctx* c, const LevelDev& L) {
 // e_c node it sits on: 1 inside, 1/2 on a face, 1/4 on an edge, 1/8 on a
 // corner.  The local operator R_s J R_s^T is read off the level operator's
 // element blocks, which are probed with the matrix-free FP64 apply (elements
-// two or more faces apart share a probe), and inverted exactly.  Levels with
+// three or more faces apart share a probe), and inverted exactly.  Levels with
 // one degree and conforming faces only.
 struct CellKey {
     long long i, j, k;
