@@ -773,8 +773,11 @@ int ensure_overlap(dg_ctx* c, int l) {
         std::vector<std::vector<int>> by_color(ncol);
         for (int e = 0; e < ne; ++e) by_color[color[e]].push_back(e);
         double *xd = nullptr, *yd = nullptr;
-        CK(cudaMalloc(&xd, sizeof(double) * N));
-        CK(cudaMalloc(&yd, sizeof(double) * N));
+        if (cudaMalloc(&xd, sizeof(double) * N) != cudaSuccess || cudaMalloc(&yd, sizeof(double) * N) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(xd);
+            return fail(DG_ERR_OOM, "device allocation failed (overlap probes)");
+        }
         std::vector<double> xh(N, 0.0), yh(N);
         int rc = DG_OK;
         cudaError_t ce = cudaSuccess;
@@ -806,7 +809,7 @@ int ensure_overlap(dg_ctx* c, int l) {
     std::vector<int> bad(ne, 0);
     auto work = [&](int e0, int e1) {
         std::vector<double> A, Ai;
-        for (int e = e0; e < e1; ++e) {
+        for (int e = e0; e < e1; ++e) try {
             const long long o = sub_off[e];
             const int m = (int)(sub_off[e + 1] - o);
             std::vector<int> el(m), lo(m);
@@ -834,16 +837,27 @@ int ensure_overlap(dg_ctx* c, int l) {
                 continue;
             }
             std::copy(Ai.begin(), Ai.end(), inv.begin() + inv_off[e]);
+        } catch (...) {   // host allocation failure: reported below, never thrown out of the thread
+            bad[e] = 2;
         }
     };
     {
         const int nt = std::max(1, std::min((int)std::thread::hardware_concurrency(), 32));
         std::vector<std::thread> th;
-        for (int t = 0; t < nt; ++t) th.emplace_back(work, (int)((long long)ne * t / nt), (int)((long long)ne * (t + 1) / nt));
+        for (int t = 0; t < nt; ++t) {
+            const int e0 = (int)((long long)ne * t / nt), e1 = (int)((long long)ne * (t + 1) / nt);
+            try {
+                th.emplace_back(work, e0, e1);
+            } catch (...) {   // no thread to be had: this share runs here
+                work(e0, e1);
+            }
+        }
         for (auto& t : th) t.join();
     }
-    for (int e = 0; e < ne; ++e)
+    for (int e = 0; e < ne; ++e) {
+        if (bad[e] == 2) return fail(DG_ERR_OOM, "overlapping Schwarz: host allocation failed");
         if (bad[e]) return fail(DG_ERR_BREAKDOWN, "overlapping Schwarz: a local operator is not positive definite");
+    }
     std::vector<float> inv32(inv.begin(), inv.end());
     Arena& Ar = c->arena;
     if (first) {
